@@ -1,0 +1,304 @@
+"""Seeded synthetic instance generators for direct SA on QUIO/HUIO.
+
+This module is deliberately free of the method's arithmetic: it only draws
+term lists (index multisets with coefficients) and variable bounds.  Both the
+CUDA path and the CPU oracle consume its output, so it must never compute an
+energy, a field, a temperature or a transition.
+
+An instance is a plain dict:
+
+    n_vars        int
+    lower, upper  int64[n_vars]              per-variable bounds l_i <= z_i <= u_i
+    term_offsets  int64[n_terms + 1]         CSR over terms
+    term_vars     int32[term_offsets[-1]]    index multiset of each term; a
+                                             repeated index is a power (z_i^2 ...)
+    coeffs        int32/int64/float32/float64[n_terms]
+    coef_type     "i32" | "i64" | "f32" | "f64"
+
+Terms may repeat a multiset and may carry a zero coefficient; merging and
+dropping are the consumer's job (Sect. 2: permutations of a multiset denote
+the same coefficient).
+
+Workload shapes (seeds fixed per workload):
+  quio_dense_small  N=32, z in [-8,7], dense symmetric int J in [-10,10],
+                    h in [-20,20], J_ii in [0,5]
+  quio_sparse_wide  N=10,000, z in [0,255], random graph with 80,000 edges
+                    (mean degree 16), fp32 J, h ~ N(0,1), J_ii ~ U[0,1]
+  huio_zipf         N=2,000, z in [-50,50], 8,000 quadratic + 20,000 cubic +
+                    5,000 quartic terms on distinct variables drawn with
+                    Zipf(1.1)-skewed popularity, int J in [-5,5]
+  fully_connected   E^FC_{p,u} of Sect. 4 (integer-scaled or float)
+  multilinear       E^ML_{p,u} of Sect. 4, periodic
+  random_interaction E^RI_{p,u} of Sect. 4, indices drawn with repetition
+"""
+from __future__ import annotations
+
+import numpy as np
+
+_NP_TYPES = {"i32": np.int32, "i64": np.int64, "f32": np.float32, "f64": np.float64}
+
+
+def _pack(n_vars, lower, upper, terms, coeffs, coef_type):
+    """terms: list of index sequences; coeffs: sequence of numbers."""
+    offs = np.zeros(len(terms) + 1, dtype=np.int64)
+    lens = np.fromiter((len(t) for t in terms), dtype=np.int64, count=len(terms))
+    np.cumsum(lens, out=offs[1:])
+    flat = np.zeros(int(offs[-1]), dtype=np.int32)
+    pos = 0
+    for t in terms:
+        flat[pos:pos + len(t)] = t
+        pos += len(t)
+    return {
+        "n_vars": int(n_vars),
+        "lower": np.asarray(lower, dtype=np.int64).copy(),
+        "upper": np.asarray(upper, dtype=np.int64).copy(),
+        "term_offsets": offs,
+        "term_vars": flat,
+        "coeffs": np.asarray(coeffs, dtype=_NP_TYPES[coef_type]).copy(),
+        "coef_type": coef_type,
+    }
+
+
+def _pack_arrays(n_vars, lower, upper, offs, flat, coeffs, coef_type):
+    return {
+        "n_vars": int(n_vars),
+        "lower": np.asarray(lower, dtype=np.int64).copy(),
+        "upper": np.asarray(upper, dtype=np.int64).copy(),
+        "term_offsets": np.asarray(offs, dtype=np.int64).copy(),
+        "term_vars": np.asarray(flat, dtype=np.int32).copy(),
+        "coeffs": np.asarray(coeffs, dtype=_NP_TYPES[coef_type]).copy(),
+        "coef_type": coef_type,
+    }
+
+
+def _quio_arrays(n, lin_idx, lin_c, diag_idx, diag_c, pi, pj, pc):
+    """Assemble linear, self-quadratic and pair terms into CSR arrays."""
+    n_lin, n_diag, n_pair = len(lin_idx), len(diag_idx), len(pi)
+    offs = np.concatenate([
+        np.zeros(1, np.int64),
+        np.arange(1, n_lin + 1, dtype=np.int64),
+        n_lin + 2 * np.arange(1, n_diag + 1, dtype=np.int64),
+        n_lin + 2 * n_diag + 2 * np.arange(1, n_pair + 1, dtype=np.int64),
+    ])
+    flat = np.concatenate([
+        np.asarray(lin_idx, np.int32),
+        np.repeat(np.asarray(diag_idx, np.int32), 2),
+        np.stack([np.asarray(pi, np.int32), np.asarray(pj, np.int32)], axis=1).reshape(-1),
+    ])
+    coeffs = np.concatenate([np.asarray(lin_c), np.asarray(diag_c), np.asarray(pc)])
+    return offs, flat, coeffs
+
+
+def quio_dense_small(seed: int = 0, n: int = 32, lo: int = -8, hi: int = 7):
+    """Dense integer QUIO: h ~ U{-20..20}, J_ii ~ U{0..5}, J_ij ~ U{-10..10} (i<j)."""
+    rng = np.random.default_rng(seed)
+    h = rng.integers(-20, 21, size=n)
+    d = rng.integers(0, 6, size=n)
+    iu, ju = np.triu_indices(n, k=1)
+    J = rng.integers(-10, 11, size=len(iu))
+    offs, flat, coeffs = _quio_arrays(n, np.arange(n), h, np.arange(n), d, iu, ju, J)
+    return _pack_arrays(n, np.full(n, lo), np.full(n, hi), offs, flat, coeffs, "i32")
+
+
+def random_graph_edges(rng, n: int, n_edges: int):
+    """Distinct undirected edges (i<j) drawn uniformly (Erdos-Renyi G(n, m))."""
+    max_edges = n * (n - 1) // 2
+    if n_edges > max_edges:
+        raise ValueError("too many edges")
+    seen = set()
+    out_i, out_j = [], []
+    while len(out_i) < n_edges:
+        need = n_edges - len(out_i)
+        a = rng.integers(0, n, size=2 * need + 16)
+        b = rng.integers(0, n, size=2 * need + 16)
+        for x, y in zip(a.tolist(), b.tolist()):
+            if x == y:
+                continue
+            if x > y:
+                x, y = y, x
+            key = x * n + y
+            if key in seen:
+                continue
+            seen.add(key)
+            out_i.append(x)
+            out_j.append(y)
+            if len(out_i) == n_edges:
+                break
+    return np.asarray(out_i, np.int64), np.asarray(out_j, np.int64)
+
+
+def quio_sparse_wide(seed: int = 1, n: int = 10_000, n_edges: int = 80_000,
+                     lo: int = 0, hi: int = 255, coef_type: str = "f32"):
+    """Sparse float QUIO on a random graph: J_ij, h_i ~ N(0,1), J_ii ~ U[0,1]."""
+    rng = np.random.default_rng(seed)
+    ei, ej = random_graph_edges(rng, n, n_edges)
+    J = rng.standard_normal(n_edges)
+    h = rng.standard_normal(n)
+    d = rng.random(n)
+    offs, flat, coeffs = _quio_arrays(n, np.arange(n), h, np.arange(n), d, ei, ej, J)
+    return _pack_arrays(n, np.full(n, lo), np.full(n, hi), offs, flat, coeffs, coef_type)
+
+
+def quio_sparse_int(seed: int, n: int, n_edges: int, lo: int, hi: int,
+                    jmax: int = 10, hmax: int = 20, dmax: int = 5):
+    """Sparse integer QUIO on a random graph (test instances)."""
+    rng = np.random.default_rng(seed)
+    ei, ej = random_graph_edges(rng, n, n_edges)
+    J = rng.integers(-jmax, jmax + 1, size=n_edges)
+    h = rng.integers(-hmax, hmax + 1, size=n)
+    d = rng.integers(0, dmax + 1, size=n)
+    offs, flat, coeffs = _quio_arrays(n, np.arange(n), h, np.arange(n), d, ei, ej, J)
+    return _pack_arrays(n, np.full(n, lo), np.full(n, hi), offs, flat, coeffs, "i32")
+
+
+def _zipf_distinct(rng, probs, size, n_terms):
+    """n_terms rows of `size` distinct variables drawn with popularity `probs`."""
+    n = len(probs)
+    cdf = np.cumsum(probs)
+    cdf /= cdf[-1]
+    out = np.empty((n_terms, size), dtype=np.int64)
+    for t in range(n_terms):
+        chosen = []
+        while len(chosen) < size:
+            v = int(np.searchsorted(cdf, rng.random(), side="right"))
+            v = min(v, n - 1)
+            if v not in chosen:
+                chosen.append(v)
+        out[t] = chosen
+    return out
+
+
+def huio_zipf(seed: int = 2, n: int = 2000, n_quad: int = 8000, n_cubic: int = 20_000,
+              n_quartic: int = 5000, lo: int = -50, hi: int = 50, cmax: int = 5,
+              zipf_s: float = 1.1, coef_type: str = "i32"):
+    """Multilinear HUIO with Zipf-skewed variable popularity (distinct vars per term)."""
+    rng = np.random.default_rng(seed)
+    rank = rng.permutation(n)                     # hubs spread over the index range
+    probs = 1.0 / np.power(rank + 1.0, zipf_s)
+    blocks, coefs = [], []
+    for size, cnt in ((2, n_quad), (3, n_cubic), (4, n_quartic)):
+        if cnt == 0:
+            continue
+        blocks.append(_zipf_distinct(rng, probs, size, cnt))
+        if coef_type in ("i32", "i64"):
+            coefs.append(rng.integers(-cmax, cmax + 1, size=cnt))
+        else:
+            coefs.append(rng.uniform(-cmax, cmax, size=cnt))
+    terms = [row for b in blocks for row in b.tolist()]
+    coeffs = np.concatenate(coefs)
+    return _pack(n, np.full(n, lo), np.full(n, hi), terms, coeffs, coef_type)
+
+
+def fully_connected(n: int, p: int, u: int, integer: bool = True):
+    """E^FC_{p,u} = -(1/u^2) sum_{i<j} z_i z_j - (1/u^p) sum_i z_i^p, z in [-u,u].
+
+    With integer=True every coefficient is multiplied by u^max(2,p) so that the
+    instance has integer coefficients; its ground energy is then
+    -u^max(2,p) N(N+1)/2.
+    """
+    terms, coefs = [], []
+    scale = u ** max(2, p)
+    for i in range(n):
+        for j in range(i + 1, n):
+            terms.append([i, j])
+            coefs.append(-(scale // (u * u)) if integer else -1.0 / (u * u))
+    for i in range(n):
+        terms.append([i] * p)
+        coefs.append(-(scale // (u ** p)) if integer else -1.0 / (u ** p))
+    return _pack(n, np.full(n, -u), np.full(n, u), terms, coefs, "i64" if integer else "f64")
+
+
+def multilinear(n: int, p: int, u: int, integer: bool = True):
+    """E^ML_{p,u} = -(1/u^p) sum_i z_i z_{i+1} ... z_{i+p-1}, periodic, z in [-u,u].
+
+    integer=True scales by u^p (coefficient -1 per term).
+    """
+    terms, coefs = [], []
+    for i in range(n):
+        terms.append([(i + q) % n for q in range(p)])
+        coefs.append(-1 if integer else -1.0 / (u ** p))
+    return _pack(n, np.full(n, -u), np.full(n, u), terms, coefs, "i64" if integer else "f64")
+
+
+def random_interaction(n: int, p: int, u: int, n_terms: int = 1000, seed: int = 0,
+                       integer: bool = False, int_scale: int = 1000):
+    """E^RI_{p,u}: n_terms terms, p indices drawn with repetition, J ~ U[-1,1] / u^p.
+
+    integer=True draws J ~ U{-int_scale..int_scale} instead (test instances).
+    """
+    rng = np.random.default_rng(seed)
+    idx = rng.integers(0, n, size=(n_terms, p))
+    if integer:
+        J = rng.integers(-int_scale, int_scale + 1, size=n_terms)
+        return _pack(n, np.full(n, -u), np.full(n, u), idx.tolist(), J, "i64")
+    J = rng.uniform(-1.0, 1.0, size=n_terms) / float(u) ** p
+    return _pack(n, np.full(n, -u), np.full(n, u), idx.tolist(), J, "f64")
+
+
+def random_small(seed: int, n: int, max_order: int, lo, hi, n_terms: int,
+                 coef_type: str = "i32", cmax: int = 5, repeat: bool = True,
+                 with_linear: bool = True):
+    """Tiny random instance for brute-force checks (indices may repeat)."""
+    rng = np.random.default_rng(seed)
+    terms, coefs = [], []
+    if with_linear:
+        for i in range(n):
+            terms.append([i])
+    for _ in range(n_terms):
+        order = int(rng.integers(1, max_order + 1))
+        if repeat:
+            t = rng.integers(0, n, size=order).tolist()
+        else:
+            order = min(order, n)
+            t = rng.choice(n, size=order, replace=False).tolist()
+        terms.append(t)
+    nt = len(terms)
+    if coef_type in ("i32", "i64"):
+        coefs = rng.integers(-cmax, cmax + 1, size=nt)
+    else:
+        coefs = rng.uniform(-cmax, cmax, size=nt)
+    lo_a = np.broadcast_to(np.asarray(lo, np.int64), (n,))
+    hi_a = np.broadcast_to(np.asarray(hi, np.int64), (n,))
+    return _pack(n, lo_a, hi_a, terms, coefs, coef_type)
+
+
+def random_bounds(seed: int, n: int, min_width: int, max_width: int, center_span: int = 10):
+    """Per-variable bounds with widths log-uniform in [min_width, max_width]."""
+    rng = np.random.default_rng(seed)
+    w = np.exp(rng.uniform(np.log(min_width), np.log(max_width), size=n)).astype(np.int64)
+    w = np.clip(w, min_width, max_width)
+    lo = rng.integers(-center_span, center_span + 1, size=n) - w // 2
+    return lo.astype(np.int64), (lo + w).astype(np.int64)
+
+
+def initial_states(seed: int, inst, n_states: int):
+    """Uniform random states inside the bounds, int32[n_states, n_vars]."""
+    rng = np.random.default_rng(seed)
+    lo, hi = inst["lower"], inst["upper"]
+    return rng.integers(lo, hi + 1, size=(n_states, inst["n_vars"])).astype(np.int32)
+
+
+# ---------------------------------------------------------------- batches
+def batch_instances(seed: int = 3, n_instances: int = 4096, n_min: int = 50, n_max: int = 2000,
+                    w_min: int = 2, w_max: int = 1024, deg_min: int = 8, deg_max: int = 64):
+    """Uneven instances: N log-uniform, range width log-uniform (lower bound 0),
+    alternating dense (full J) and sparse (degree U{deg_min..deg_max}); fp32
+    J, h ~ N(0,1), J_ii ~ U[0,1].  Returns a list of instance dicts."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for idx in range(n_instances):
+        n = int(np.exp(rng.uniform(np.log(n_min), np.log(n_max))))
+        w = int(np.exp(rng.uniform(np.log(w_min), np.log(w_max))))
+        dense = (idx % 2 == 0)
+        if dense:
+            iu, ju = np.triu_indices(n, k=1)
+        else:
+            deg = int(rng.integers(deg_min, deg_max + 1))
+            m = min(n * deg // 2, n * (n - 1) // 2)
+            iu, ju = random_graph_edges(rng, n, m)
+        J = rng.standard_normal(len(iu)).astype(np.float32)
+        h = rng.standard_normal(n).astype(np.float32)
+        d = rng.random(n).astype(np.float32)
+        offs, flat, coeffs = _quio_arrays(n, np.arange(n), h, np.arange(n), d, iu, ju, J)
+        out.append(_pack_arrays(n, np.zeros(n), np.full(n, w - 1), offs, flat, coeffs, "f32"))
+    return out
