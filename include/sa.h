@@ -1,0 +1,216 @@
+/*
+ * sa.h -- C ABI of the GB300 (sm_103a) library for direct simulated annealing
+ * (SA) on quadratic and higher-order unconstrained integer optimization
+ * (QUIO / HUIO), after K. Suzuki, arXiv:2511.17245.
+ *
+ * The library runs the single-variable update sweep of Sect. 3 on the GPU:
+ * for each integer variable in index order it evaluates the energy change of
+ * a candidate value from cached per-replica coefficients (Eq. energy_diff_quad
+ * for QUIO, Eq. energy_diff_poly for HUIO), draws the move by Metropolis
+ * (Sect. 3.3.1), heat bath (Eq. prob_heatbath, with the O(1) inverse transform
+ * of Eq. inverse_prob for multilinear variables) or optimal-transition
+ * Metropolis (Eq. eq_opt_trans), and updates the cached coefficients of the
+ * variables that share a term with the moved one (Eq. energy_diff_upd).
+ *
+ * Conventions for every entry point
+ *   - Plain C types only.  `stream` is a cudaStream_t passed as void*
+ *     (NULL = the legacy default stream).  All work is enqueued on it.
+ *   - Pointers marked "host or device" are classified with
+ *     cudaPointerGetAttributes.  When every output is device memory the call
+ *     is asynchronous on `stream`; when any output is host memory the call
+ *     copies through device temporaries and synchronises `stream` before it
+ *     returns.
+ *   - The caller owns every buffer it passes; the library copies what it needs
+ *     and keeps no pointer after the call returns.  A model owns its device
+ *     copy until sa_model_destroy.
+ *   - Errors are returned as sa_status; nothing aborts the process.  A
+ *     human-readable message for the last failing call on the calling thread
+ *     is available from sa_last_error().
+ *   - A model lives on the CUDA device that was current when it was created;
+ *     calls that use it must run with that device current.
+ */
+#ifndef SA_GB300_H
+#define SA_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SA_OK = 0,
+    SA_ERR_INVALID = 1,      /* malformed argument, bound or term list       */
+    SA_ERR_OVERFLOW = 2,     /* integer model could overflow int64 (see below) */
+    SA_ERR_UNSUPPORTED = 3,  /* valid request outside what the kernels cover */
+    SA_ERR_OOM = 4,          /* device allocation failed                     */
+    SA_ERR_CUDA = 5,         /* a CUDA runtime call or launch failed         */
+    SA_ERR_TIMEOUT = 6,      /* a bounded wait gave up                       */
+    SA_ERR_BUSY = 7          /* the resource is in use                       */
+} sa_status;
+
+typedef enum {
+    SA_COEF_I32 = 0,         /* int32_t coefficients: exact int64 arithmetic   */
+    SA_COEF_I64 = 1,         /* int64_t coefficients: exact int64 arithmetic   */
+    SA_COEF_F32 = 2,         /* float coefficients: fp32 fields, FP64 refresh  */
+    SA_COEF_F64 = 3          /* double coefficients: fp32 fields, FP64 refresh */
+} sa_coef_type;
+
+typedef enum {
+    SA_METROPOLIS = 0,       /* Sect. 3.3.1 */
+    SA_HEAT_BATH = 1,        /* Sect. 3.3.2, Eqs. prob_heatbath, inverse_prob */
+    SA_OPT_METROPOLIS = 2    /* Sect. 3.3.3, Eq. eq_opt_trans */
+} sa_rule;
+
+typedef struct sa_model sa_model;   /* opaque, owned by the library */
+
+/*
+ * sa_model_create -- compile a QUIO/HUIO objective (Eqs. def_QUIO, def_HUIO)
+ * into a device-resident model.
+ *
+ *   out           receives the new model; *out is NULL on failure.
+ *   n_vars        N >= 1.
+ *   lower, upper  host int64[N]: bounds l_i <= z_i <= u_i (Sect. 2).  Each
+ *                 bound must fit int32 and u_i - l_i must be < 2^31.
+ *   n_terms       number of terms (>= 0).
+ *   term_offsets  host int64[n_terms + 1], term_offsets[0] = 0, non-decreasing:
+ *                 term t is term_vars[term_offsets[t] .. term_offsets[t+1]).
+ *   term_vars     host int32: each term's index multiset.  Order is irrelevant;
+ *                 a repeated index is a power (z_k^m); a one-index term is a
+ *                 linear term; an empty term is a constant.
+ *   coeffs        host array of n_terms values of `coef_type`.
+ *
+ * Terms with equal multisets are merged by summing (Sect. 2); terms whose
+ * merged coefficient is exactly zero are dropped.  Integer models are checked
+ * against int64 overflow: with z^max_i = max(|l_i|, |u_i|, 1), the sum over
+ * terms of |J| prod z^max must stay below 2^62, and for every variable k the
+ * bound sum_m a~_k^(m) * 2 (z^max_k)^m (a~ as in Sect. 3.4) must stay below
+ * 2^62; otherwise SA_ERR_OVERFLOW.  NaN/Inf coefficients, out-of-range indices
+ * and l > u give SA_ERR_INVALID; exponents above 63 give SA_ERR_UNSUPPORTED.
+ */
+sa_status sa_model_create(sa_model** out, int32_t n_vars, const int64_t* lower, const int64_t* upper,
+                          int64_t n_terms, const int64_t* term_offsets, const int32_t* term_vars,
+                          const void* coeffs, sa_coef_type coef_type);
+
+/* Releases the model and its device memory.  NULL is ignored.  The caller must
+ * make sure no enqueued work still uses the model. */
+void sa_model_destroy(sa_model* model);
+
+typedef struct {
+    int32_t n_vars;
+    int32_t is_float;         /* 1 for SA_COEF_F32/F64 models                   */
+    int32_t is_quadratic;     /* every merged term has total degree <= 2        */
+    int32_t max_exponent;     /* largest power of one variable in one term      */
+    int32_t max_order;        /* largest total degree of a term                 */
+    int32_t all_multilinear;  /* every variable appears with exponent 1 only    */
+    int64_t n_terms;          /* merged, non-zero, non-constant terms           */
+    int64_t n_links;          /* QUIO: adjacency entries; HUIO: incidences      */
+    int32_t n_levels;         /* dependency levels of one sweep (see run)       */
+    int32_t max_width;        /* largest u_k - l_k                              */
+    int64_t device_bytes;     /* device memory held by the model                */
+} sa_model_info;
+
+/* Fills `info` with a description of the compiled model. */
+sa_status sa_model_get_info(const sa_model* model, sa_model_info* info);
+
+/*
+ * sa_default_temperatures -- initial and final temperature from the model
+ * alone (Sect. 3.4): T_max = -dE_max / ln(1/2) with
+ * dE_max ~ max_k sum_{m in Omega_k} a~_k^(m) (u_k - l_k)^m (Eq. eq_temp_init),
+ * T_min = -dE_min / ln(0.001) with dE_min ~ the smallest |J| over all terms.
+ * Host-only; both outputs are host pointers.
+ */
+sa_status sa_default_temperatures(const sa_model* model, double* t_max, double* t_min);
+
+/* Optional per-run report, filled on the host after the run (forces a
+ * synchronisation of the stream). */
+typedef struct {
+    double max_refresh_drift;     /* float models: max |fp32 field - FP64 field| seen at refreshes */
+    int32_t replicas_per_block;   /* launch shape chosen for the sweep kernel */
+    int32_t threads_per_replica;
+    int32_t state_in_global;      /* 1 if the per-replica state lived in global memory */
+    int32_t shared_bytes;         /* dynamic shared memory per block */
+    int32_t blocks;               /* grid size of the sweep kernel */
+    int32_t n_levels;
+    float kernel_ms;              /* device time of the sweep kernel (CUDA events) */
+    int32_t _reserved;
+} sa_run_report;
+
+/* Run flags */
+#define SA_FLAG_STATE_IN_GLOBAL 0x1   /* keep per-replica state in global memory even if it fits on chip */
+
+typedef struct {
+    int32_t rule;                 /* sa_rule                                              */
+    int32_t n_sweeps;             /* S >= 1                                               */
+    int32_t n_replicas;           /* R >= 1 independent SA runs ("samples", Sect. 4)      */
+    int32_t refresh_interval;     /* float models: sweeps between FP64 refreshes; 0 -> 50 */
+    uint64_t seed;                /* Philox key = (lo32(seed), hi32(seed))               */
+    double t_max, t_min;          /* geometric schedule of Sect. 3.1; both <= 0 -> Sect. 3.4 defaults */
+    const double* temperatures;   /* optional host double[S]: explicit T per sweep       */
+    const int32_t* init_states;   /* optional int32[R][N] (host or device); else uniform random */
+    uint32_t instance_id;         /* fourth Philox counter word (default 0)              */
+    int32_t replicas_per_block;   /* launch shape override, 0 = automatic                */
+    int32_t threads_per_replica;  /* launch shape override (multiple of 32), 0 = automatic */
+    int32_t flags;                /* SA_FLAG_*                                           */
+    int32_t* trace;               /* optional device int32[S][trace_replicas][N]: value of z_k after
+                                     every attempt of replicas < trace_replicas (testing aid) */
+    int32_t trace_replicas;
+    int32_t _pad0;
+    void* energy_trace;           /* optional device int64 (integer models) or double
+                                     (float models) [S][R]: energy after every sweep     */
+    sa_run_report* report;        /* optional host report                                */
+} sa_run_params;
+
+/*
+ * sa_run -- R independent SA runs of Sect. 3.1 on one model.
+ *
+ * Random numbers: one Philox4x32-10 block per attempt with counter
+ * (k, s, r, instance_id) and key (lo32(seed), hi32(seed)); the initial state
+ * uses s = 0xFFFFFFFF.  U = (x >> 8) 2^-24 in [0,1), Uc = ((x >> 8) + 1) 2^-24
+ * in (0,1], pick(x, M) = (x M) >> 32.  Sweep s (0-based) runs at
+ * T_s = T_max (T_min/T_max)^(s/(S-1)), with beta_s = fp32(1/T_s), and OTM
+ * ratio r_s = fp32(s)/fp32(S-1).
+ *
+ *   out_states    int32[R][N] (host or device): final z, one row per replica.
+ *   out_energies  int64[R] for integer models, double[R] for float models
+ *                 (host or device): final energy (exact for integer models;
+ *                 FP64 recomputation from the final state for float models).
+ *   out_accepts   optional uint64[R] (host or device): number of attempts that
+ *                 changed the variable.
+ *
+ * Visiting order: within a sweep variables are updated in index order
+ * (Sect. 3.1).  The kernels run the updates of variables that share no term
+ * concurrently when they form a dependency level; this reproduces the
+ * sequential trajectory exactly for integer models.
+ *
+ * Errors: SA_ERR_INVALID for bad parameters, SA_ERR_UNSUPPORTED for OTM on a
+ * variable with exponent above 4 (Sect. 3.3.3 implements degree <= 4),
+ * SA_ERR_OOM / SA_ERR_CUDA for device failures.
+ */
+sa_status sa_run(const sa_model* model, const sa_run_params* params, int32_t* out_states,
+                 void* out_energies, uint64_t* out_accepts, void* stream);
+
+/*
+ * sa_energy -- E(z) of Eq. def_HUIO for n_states states.
+ *
+ *   states    int32[n_states][N] (host or device), each value inside its bounds.
+ *   energies  int64[n_states] for integer models, double[n_states] for float
+ *             models (host or device).
+ * Values outside the bounds give SA_ERR_INVALID (checked on the device; the call
+ * then synchronises the stream).
+ */
+sa_status sa_energy(const sa_model* model, const int32_t* states, int64_t n_states, void* energies,
+                    void* stream);
+
+/* Message of the last failed call on the calling thread ("" if none). */
+const char* sa_last_error(void);
+
+/* Library version string. */
+const char* sa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SA_GB300_H */

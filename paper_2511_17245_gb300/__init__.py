@@ -1,0 +1,67 @@
+"""GB300 (sm_103a) direct simulated annealing for QUIO/HUIO (arXiv:2511.17245).
+
+The compute path is the CUDA library libsa_gb300.so behind the C ABI of
+include/sa.h; `_lib` is its ctypes binding.  `Model` below is a convenience
+wrapper that allocates torch tensors for the outputs and forwards to the
+C entry points; it performs no arithmetic of the method.
+"""
+from __future__ import annotations
+
+from . import _lib
+from ._lib import (RULES, SAError, make_params, sa_default_temperatures, sa_energy, sa_last_error,
+                   sa_model_create, sa_model_destroy, sa_model_get_info, sa_run, sa_run_report, sa_version)
+
+__all__ = ["Model", "RULES", "SAError", "make_params", "sa_default_temperatures", "sa_energy", "sa_last_error",
+           "sa_model_create", "sa_model_destroy", "sa_model_get_info", "sa_run", "sa_run_report", "sa_version"]
+
+
+class Model:
+    """Owns one sa_model handle built from an instance dict (see workloads)."""
+
+    def __init__(self, inst):
+        self.n = int(inst["n_vars"])
+        self.handle = sa_model_create(inst["n_vars"], inst["lower"], inst["upper"], inst["term_offsets"],
+                                      inst["term_vars"], inst["coeffs"], inst["coef_type"])
+        self.info = sa_model_get_info(self.handle)
+        self.is_float = bool(self.info["is_float"])
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sa_model_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def default_temperatures(self):
+        return sa_default_temperatures(self.handle)
+
+    def run(self, rule="metropolis", n_sweeps=1000, n_replicas=64, seed=0, device="cuda", stream=None,
+            report=False, **kw):
+        """Runs sa_run into freshly allocated torch tensors; returns a dict."""
+        import torch
+        states = torch.empty((n_replicas, self.n), dtype=torch.int32, device=device)
+        energies = torch.empty(n_replicas, dtype=torch.float64 if self.is_float else torch.int64, device=device)
+        accepts = torch.empty(n_replicas, dtype=torch.int64, device=device)
+        rep = sa_run_report() if report else None
+        params = make_params(rule=rule, n_sweeps=n_sweeps, n_replicas=n_replicas, seed=seed, report=rep, **kw)
+        if stream is None and str(device).startswith("cuda"):
+            stream = torch.cuda.current_stream().cuda_stream
+        sa_run(self.handle, params, states, energies, accepts, stream)
+        out = {"states": states, "energies": energies, "accepts": accepts}
+        if rep is not None:
+            out["report"] = {f: getattr(rep, f) for f, _ in rep._fields_}
+        return out
+
+    def energy(self, states, stream=None):
+        import torch
+        n = states.shape[0]
+        dev = states.device
+        out = torch.empty(n, dtype=torch.float64 if self.is_float else torch.int64, device=dev)
+        if stream is None and dev.type == "cuda":
+            stream = torch.cuda.current_stream().cuda_stream
+        sa_energy(self.handle, states.contiguous(), n, out, stream)
+        return out

@@ -1,0 +1,748 @@
+// sweep.cuh -- the single-variable update sweep of direct SA (arXiv:2511.17245,
+// Sect. 3) for sm_103a.
+//
+// Layout and parallel structure
+//   * One group of `tpr` threads (whole warps) owns one replica (an
+//     independent SA run).  A block holds `rpc` such groups; each group
+//     synchronises on its own named barrier (id 1 + slot).
+//   * A replica's state -- the offsets z_k - l_k (1, 2 or 4 bytes) and the
+//     cached coefficients (QUIO: f_k = J_k + sum_{i != k} J_ik z_i, the
+//     paper's c^(1)_k minus 2 J_kk z_k; HUIO: a_k^(m) of Eq. energy_diff_poly)
+//     -- lives in shared memory when it fits, else in a global slab.
+//   * Sequential visit order (Sect. 3.1) is kept exactly: the host splits the
+//     index sequence 0..N-1 into dependency levels (level(k) = 1 + max level
+//     of the neighbours j < k that share a term with k).  Variables of one
+//     level share no term, so their decisions read disjoint state and their
+//     cache updates commute; the group runs a level in parallel and
+//     barriers between levels.  For integer models this reproduces the
+//     sequential trajectory bit for bit.
+//   * Per attempt: one Philox4x32-10 block with counter (k, s, r, instance).
+//
+// Decision arithmetic (shared convention with the CPU oracle):
+//   Metropolis / OTM acceptance: dE <= 0, or U(x1) < expf(-fp32(dE) * beta_s).
+//   Heat bath: weights expf(-fp32(dE_v - dE_min) * beta_s), compensated fp32
+//   sums, smallest v with C_v >= Uc(x0) * C_total; multilinear variables use
+//   the inverse transform of Eq. inverse_prob.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "sa_internal.h"
+
+namespace sa {
+namespace dev {
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3" (SC'11).
+struct Words4 {
+    uint32_t x0, x1, x2, x3;
+};
+
+__device__ __forceinline__ Words4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo0 = 0xD2511F53u * c0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t lo1 = 0xCD9E8D57u * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ k0;
+        const uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return {c0, c1, c2, c3};
+}
+
+__device__ __forceinline__ float unit_open_right(uint32_t x) { return __uint2float_rn(x >> 8) * 0x1p-24f; }
+__device__ __forceinline__ float unit_open_left(uint32_t x) { return __uint2float_rn((x >> 8) + 1u) * 0x1p-24f; }
+__device__ __forceinline__ uint32_t pick_below(uint32_t x, uint32_t m) { return __umulhi(x, m); }
+
+// ------------------------------------------------------------------ numeric traits
+template <class F>
+struct Num;
+template <>
+struct Num<long long> {
+    using Acc = long long;                 // energy accumulator
+    static constexpr bool is_float = false;
+    __device__ static float to_f(long long v) { return __ll2float_rn(v); }
+};
+template <>
+struct Num<float> {
+    using Acc = double;
+    static constexpr bool is_float = true;
+    __device__ static float to_f(float v) { return v; }
+};
+
+__device__ __forceinline__ void named_bar(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+__device__ __forceinline__ void atomic_add_field(float* p, float v) { atomicAdd(p, v); }
+__device__ __forceinline__ void atomic_add_field(long long* p, long long v) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(v));
+}
+
+// Floor division for int64 with positive divisor.
+__device__ __forceinline__ long long floor_div(long long a, long long b) {
+    long long q = a / b;
+    if ((a % b != 0) && (a < 0)) --q;
+    return q;
+}
+
+// ------------------------------------------------------------------ model accessors
+template <class F>
+struct Coef;
+template <>
+struct Coef<long long> {
+    __device__ static long long adj(const DevModel& m, int i) { return m.adj_i[i]; }
+    __device__ static long long lin(const DevModel& m, int k) { return m.lin_i[k]; }
+    __device__ static long long diag(const DevModel& m, int k) { return m.diag_i[k]; }
+    __device__ static long long aconst(const DevModel& m, int s) { return m.aconst_i[s]; }
+    __device__ static long long tcoef(const DevModel& m, int t) { return m.tcoef_i[t]; }
+};
+template <>
+struct Coef<float> {
+    __device__ static float adj(const DevModel& m, int i) { return __ldg(m.adj_f + i); }
+    __device__ static float lin(const DevModel& m, int k) { return __ldg(m.lin_f + k); }
+    __device__ static float diag(const DevModel& m, int k) { return __ldg(m.diag_f + k); }
+    __device__ static float aconst(const DevModel& m, int s) { return __ldg(m.aconst_f + s); }
+    __device__ static float tcoef(const DevModel& m, int t) { return __ldg(m.tcoef_f + t); }
+};
+
+// Integer power by repeated multiplication (exponents are small).
+template <class T>
+__device__ __forceinline__ T ipow(T x, int e) {
+    T r = T(1);
+    for (int i = 0; i < e; ++i) r *= x;
+    return r;
+}
+
+// ------------------------------------------------------------------ energy change
+// QUIO (Eq. energy_diff_quad): dE(v) = (v - z) * (f + J_kk (v + z)), f = c1 - 2 J_kk z.
+template <class F>
+__device__ __forceinline__ F quio_delta(F f, F d, long long z, long long v) {
+    if constexpr (Num<F>::is_float) {
+        const float dz = (float)(v - z);
+        return dz * fmaf(d, (float)(v + z), f);
+    } else {
+        return (v - z) * (f + d * (v + z));
+    }
+}
+
+// HUIO (Eq. energy_diff_poly): dE(v) = sum_{m in Omega_k} a^(m) (v^m - z^m).
+template <class F>
+__device__ __forceinline__ F huio_delta(const F* a_slots, uint64_t omega, long long z, long long v) {
+    F acc = F(0);
+    if constexpr (Num<F>::is_float) {
+        float pv = 1.f, pz = 1.f;
+        const float vf = (float)v, zf = (float)z;
+        int slot = 0;
+        uint64_t msk = omega >> 1;
+        while (msk) {
+            pv *= vf;
+            pz *= zf;
+            if (msk & 1ull) acc = fmaf(a_slots[slot++], pv - pz, acc);
+            msk >>= 1;
+        }
+    } else {
+        long long pv = 1, pz = 1;
+        int slot = 0;
+        uint64_t msk = omega >> 1;
+        while (msk) {
+            pv *= v;
+            pz *= z;
+            if (msk & 1ull) acc += a_slots[slot++] * (pv - pz);
+            msk >>= 1;
+        }
+    }
+    return acc;
+}
+
+template <class F>
+__device__ __forceinline__ bool le_zero(F x) { return x <= F(0); }
+
+// Metropolis acceptance of Sect. 3.3.1 in the shared fp32 convention.
+template <class F>
+__device__ __forceinline__ bool metropolis_accept(F de, uint32_t xu, float beta) {
+    if (de <= F(0)) return true;
+    const float x = Num<F>::to_f(de) * beta;
+    const float p = expf(-x);
+    return unit_open_right(xu) < p;
+}
+
+// ------------------------------------------------------------------ per-variable view
+// Everything the decision of variable k needs, for either model kind.
+template <class F, int KIND>
+struct VarView;
+
+template <class F>
+struct VarView<F, KIND_QUIO> {
+    F f, d;
+    __device__ F delta(long long z, long long v) const { return quio_delta<F>(f, d, z, v); }
+    __device__ bool linear() const { return d == F(0); }
+    __device__ F lin_coef() const { return f; }
+    __device__ int max_exp() const { return d == F(0) ? 1 : 2; }
+    __device__ F coef(int m) const { return m == 1 ? f : (m == 2 ? d : F(0)); }
+};
+
+template <class F>
+struct VarView<F, KIND_HUIO> {
+    const F* a;
+    uint64_t omega;
+    __device__ F delta(long long z, long long v) const { return huio_delta<F>(a, omega, z, v); }
+    __device__ bool linear() const { return (omega & ~2ull) == 0; }
+    __device__ F lin_coef() const { return (omega & 2ull) ? a[0] : F(0); }
+    __device__ int max_exp() const { return omega ? 63 - __clzll(omega) : 0; }
+    // coefficient of z^m (0 if absent)
+    __device__ F coef(int m) const {
+        if (!((omega >> m) & 1ull)) return F(0);
+        const uint64_t below = omega & ((1ull << m) - 1ull);
+        return a[__popcll(below >> 1)];
+    }
+};
+
+// ------------------------------------------------------------------ OTM argmin
+// argmin over v in [lo, lo+width], v != z, of dE(v); ties to the smallest v.
+// Candidate set: lo, hi, z-1, z+1 and the integers around every local minimum
+// of the continuous polynomial (exact for degree <= 2; for degree 3 and 4 the
+// critical points are bracketed on the monotone pieces of P' and a window of
+// integers around each is evaluated exactly).
+template <class F, int KIND>
+struct ArgminState {
+    long long best_v;
+    F best;
+    bool have;
+    __device__ void offer(const VarView<F, KIND>& vv, long long z, long long lo, long long hi, long long v) {
+        if (v < lo || v > hi || v == z) return;
+        const F de = vv.delta(z, v);
+        if (!have || de < best || (de == best && v < best_v)) {
+            best = de;
+            best_v = v;
+            have = true;
+        }
+    }
+};
+
+template <class F, int KIND>
+__device__ long long opt_argmin(const VarView<F, KIND>& vv, long long z, long long lo, long long hi) {
+    ArgminState<F, KIND> st{0, F(0), false};
+    st.offer(vv, z, lo, hi, lo);
+    st.offer(vv, z, lo, hi, hi);
+    st.offer(vv, z, lo, hi, z - 1);
+    st.offer(vv, z, lo, hi, z + 1);
+    const int me = vv.max_exp();
+    if (me == 2) {
+        const F a1 = vv.coef(1), a2 = vv.coef(2);
+        if (a2 > F(0)) {
+            long long q;
+            if constexpr (Num<F>::is_float) {
+                float qv = floorf(-a1 / (2.f * a2));
+                qv = fminf(fmaxf(qv, (float)lo - 1.f), (float)hi + 1.f);
+                q = (long long)qv;
+            } else {
+                q = floor_div(-a1, 2 * a2);
+            }
+            st.offer(vv, z, lo, hi, q);
+            st.offer(vv, z, lo, hi, q + 1);
+        }
+    } else if (me >= 3) {
+        // P'(x) = c0 + c1 x + c2 x^2 + c3 x^3 in double; pieces between the
+        // roots of P'' are monotone; bisect each sign change on the integers.
+        const double c0 = (double)vv.coef(1), c1 = 2.0 * (double)vv.coef(2);
+        const double c2 = 3.0 * (double)vv.coef(3), c3 = 4.0 * (double)vv.coef(4);
+        auto dp = [&](double x) { return ((c3 * x + c2) * x + c1) * x + c0; };
+        double brk[4];
+        int nb = 0;
+        brk[nb++] = (double)lo;
+        // roots of P''(x) = c1 + 2 c2 x + 3 c3 x^2
+        const double qa = 3.0 * c3, qb = 2.0 * c2, qc = c1;
+        if (qa != 0.0) {
+            const double disc = qb * qb - 4.0 * qa * qc;
+            if (disc > 0.0) {
+                const double sq = sqrt(disc);
+                const double t = -0.5 * (qb + (qb >= 0 ? sq : -sq));
+                double r1 = t / qa, r2 = (t != 0.0) ? qc / t : r1;
+                if (r1 > r2) { const double tmp = r1; r1 = r2; r2 = tmp; }
+                if (r1 > (double)lo && r1 < (double)hi) brk[nb++] = r1;
+                if (r2 > (double)lo && r2 < (double)hi && r2 != r1) brk[nb++] = r2;
+            }
+        } else if (qb != 0.0) {
+            const double r = -qc / qb;
+            if (r > (double)lo && r < (double)hi) brk[nb++] = r;
+        }
+        brk[nb++] = (double)hi;
+        for (int p = 0; p + 1 < nb; ++p) {
+            long long a = (long long)floor(brk[p]), b = (long long)ceil(brk[p + 1]);
+            if (a < lo) a = lo;
+            if (b > hi) b = hi;
+            // window around each break point
+            for (long long w = -2; w <= 2; ++w) st.offer(vv, z, lo, hi, a + w);
+            const double fa = dp((double)a), fb = dp((double)b);
+            if (fa < 0.0 && fb > 0.0) {          // P' increases through zero: local minimum
+                long long L = a, H = b;          // dp(L) < 0 <= dp(H)
+                while (H - L > 1) {
+                    const long long mid = L + (H - L) / 2;
+                    if (dp((double)mid) < 0.0) L = mid; else H = mid;
+                }
+                for (long long w = -2; w <= 3; ++w) st.offer(vv, z, lo, hi, L + w);
+            }
+        }
+    }
+    return st.have ? st.best_v : z;
+}
+
+// ------------------------------------------------------------------ heat bath
+// Explicit inverse CDF over all u-l+1 values (Eq. prob_heatbath).  Three passes
+// over the candidates: minimum dE, compensated total, compensated search.
+template <class F, int KIND>
+__device__ long long heat_bath_general(const VarView<F, KIND>& vv, long long z, long long lo, uint32_t width,
+                                       uint32_t xu, float beta) {
+    F mn = F(0);  // dE = 0 at the current value
+    for (uint32_t i = 0; i <= width; ++i) {
+        const F de = vv.delta(z, lo + (long long)i);
+        mn = de < mn ? de : mn;
+    }
+    float sum = 0.f, comp = 0.f;
+    for (uint32_t i = 0; i <= width; ++i) {
+        const F de = vv.delta(z, lo + (long long)i);
+        const float w = expf(-(Num<F>::to_f(de - mn) * beta));
+        const float y = w - comp;
+        const float t = sum + y;
+        comp = (t - sum) - y;
+        sum = t;
+    }
+    const float thr = unit_open_left(xu) * sum;
+    float run = 0.f, c2 = 0.f;
+    for (uint32_t i = 0; i <= width; ++i) {
+        const F de = vv.delta(z, lo + (long long)i);
+        const float w = expf(-(Num<F>::to_f(de - mn) * beta));
+        const float y = w - c2;
+        const float t = run + y;
+        c2 = (t - run) - y;
+        run = t;
+        if (run >= thr) return lo + (long long)i;
+    }
+    return lo + (long long)width;
+}
+
+// Multilinear variable, dE = a (v - z): P(i) proportional to exp(-lambda i) on
+// i = 0..n-1, lambda = a beta; inverse transform of Eq. inverse_prob, written
+// with expm1/log1p; the pick is i = ceil(X) - 1 with X solving P_sum = Uc.
+__device__ __forceinline__ long long heat_bath_linear(float a, long long lo, uint32_t width, uint32_t xu,
+                                                      float beta) {
+    const float U = unit_open_left(xu);
+    const float lam = a * beta;
+    long long i;
+    if (width < (1u << 24)) {
+        const float n = (float)(width + 1u);
+        float X;
+        if (lam == 0.f) {
+            X = U * n;
+        } else if (lam > 0.f) {
+            X = -log1pf(U * expm1f(-lam * n)) / lam;
+        } else {
+            const float mu = -lam;
+            X = n + logf(U + (1.f - U) * expf(-mu * n)) / mu;
+        }
+        i = (long long)ceilf(X) - 1;
+    } else {
+        const double n = (double)width + 1.0, Ud = (double)U, l = (double)lam;
+        double X;
+        if (l == 0.0) X = Ud * n;
+        else if (l > 0.0) X = -log1p(Ud * expm1(-l * n)) / l;
+        else X = n + log(Ud + (1.0 - Ud) * exp(l * n)) / (-l);
+        i = (long long)ceil(X) - 1;
+    }
+    if (i < 0) i = 0;
+    if (i > (long long)width) i = (long long)width;
+    return lo + i;
+}
+
+// ------------------------------------------------------------------ cache recompute
+// QUIO: f_k = lin_k + sum_j J_kj z_j (exact int64, or FP64 then cast to fp32).
+// Returns this thread's share of E: sum_k z_k (lin_k + diag_k z_k) and
+// sum_k z_k (f_k - lin_k) (twice the pair energy).
+template <class F, class Z>
+__device__ void quio_recompute(const DevModel& m, const Z* zs, F* cache, int t, int tpr, bool measure,
+                               float& drift, typename Num<F>::Acc& e_ld, typename Num<F>::Acc& e_pair2) {
+    for (int k = t; k < m.n; k += tpr) {
+        const VarMeta mt = m.meta[k];
+        const long long zk = (long long)mt.lo + (long long)zs[k];
+        if constexpr (Num<F>::is_float) {
+            double f = m.lin_d[k];
+            for (int e = mt.link_begin; e < mt.link_begin + mt.link_len; ++e) {
+                const int j = m.adj_col[e];
+                f += m.adj_d[e] * (double)((long long)m.meta[j].lo + (long long)zs[j]);
+            }
+            const float ff = (float)f;
+            if (measure) drift = fmaxf(drift, (float)fabs((double)cache[k] - f));
+            cache[k] = ff;
+            e_ld += (double)zk * (m.lin_d[k] + m.diag_d[k] * (double)zk);
+            e_pair2 += (double)zk * (f - m.lin_d[k]);
+        } else {
+            long long f = m.lin_i[k];
+            for (int e = mt.link_begin; e < mt.link_begin + mt.link_len; ++e) {
+                const int j = m.adj_col[e];
+                f += m.adj_i[e] * ((long long)m.meta[j].lo + (long long)zs[j]);
+            }
+            cache[k] = f;
+            e_ld += zk * (m.lin_i[k] + m.diag_i[k] * zk);
+            e_pair2 += zk * (f - m.lin_i[k]);
+        }
+    }
+}
+
+// HUIO: a_k^(m) = J_{k..k} + sum over interaction terms t containing k with
+// exponent m of J_t prod_{i in t, i != k} z_i^{e_i}.  Thread k owns its slots.
+// Energy share: single-variable terms of the owned variables plus the
+// interaction terms t = t0, t0 + tpr, ...
+template <class F, class Z>
+__device__ void huio_recompute(const DevModel& m, const Z* zs, F* cache, int t, int tpr, bool measure,
+                               float& drift, typename Num<F>::Acc& e_self, typename Num<F>::Acc& e_terms) {
+    using Acc = typename Num<F>::Acc;
+    for (int k = t; k < m.n; k += tpr) {
+        const VarMeta mt = m.meta[k];
+        const long long zk = (long long)mt.lo + (long long)zs[k];
+        const int base = m.slot_base[k];
+        const uint64_t om = m.omega[k];
+        const int nsl = __popcll(om);
+        // start from the constants, accumulate interaction contributions
+        Acc acc[8];
+        const int nloc = nsl < 8 ? nsl : 8;
+        for (int q = 0; q < nloc; ++q) {
+            if constexpr (Num<F>::is_float) acc[q] = m.aconst_d[base + q];
+            else acc[q] = m.aconst_i[base + q];
+        }
+        for (int q = nloc; q < nsl; ++q) {
+            if constexpr (Num<F>::is_float) cache[base + q] = (F)m.aconst_d[base + q];
+            else cache[base + q] = m.aconst_i[base + q];
+        }
+        for (int e = mt.link_begin; e < mt.link_begin + mt.link_len; ++e) {
+            const int tt = m.inc_term[e];
+            const int ek = m.inc_exp[e];
+            Acc prod;
+            if constexpr (Num<F>::is_float) prod = m.tcoef_d[tt];
+            else prod = m.tcoef_i[tt];
+            for (int p = m.term_ptr[tt]; p < m.term_ptr[tt + 1]; ++p) {
+                const int v = m.mem_var[p];
+                if (v == k) continue;
+                const long long zv = (long long)m.meta[v].lo + (long long)zs[v];
+                prod *= ipow<Acc>((Acc)zv, m.mem_exp[p]);
+            }
+            const int q = __popcll((om & ((1ull << ek) - 1ull)) >> 1);
+            if (q < 8) acc[q] += prod;
+            else cache[base + q] += (F)prod;
+        }
+        for (int q = 0; q < nloc; ++q) {
+            if constexpr (Num<F>::is_float) {
+                if (measure) drift = fmaxf(drift, (float)fabs((double)cache[base + q] - acc[q]));
+                cache[base + q] = (float)acc[q];
+            } else {
+                cache[base + q] = acc[q];
+            }
+        }
+        // single-variable terms' energy: sum_m aconst z^m
+        uint64_t msk = om >> 1;
+        Acc pz = 1;
+        int q = 0;
+        while (msk) {
+            pz *= (Acc)zk;
+            if (msk & 1ull) {
+                if constexpr (Num<F>::is_float) e_self += m.aconst_d[base + q] * pz;
+                else e_self += m.aconst_i[base + q] * pz;
+                ++q;
+            }
+            msk >>= 1;
+        }
+    }
+    for (int tt = t; tt < m.n_iterms; tt += tpr) {
+        Acc prod;
+        if constexpr (Num<F>::is_float) prod = m.tcoef_d[tt];
+        else prod = m.tcoef_i[tt];
+        for (int p = m.term_ptr[tt]; p < m.term_ptr[tt + 1]; ++p) {
+            const int v = m.mem_var[p];
+            const long long zv = (long long)m.meta[v].lo + (long long)zs[v];
+            prod *= ipow<Acc>((Acc)zv, m.mem_exp[p]);
+        }
+        e_terms += prod;
+    }
+}
+
+// ------------------------------------------------------------------ cache update
+// QUIO (Sect. 3.2): z_s += dz changes f_j by J_sj dz for every neighbour j.
+template <class F>
+__device__ __forceinline__ void quio_update_range(const DevModel& m, F* cache, int begin, int end, int stride,
+                                                  long long dz) {
+    if constexpr (Num<F>::is_float) {
+        const float d = (float)dz;
+        for (int e = begin; e < end; e += stride) atomic_add_field(cache + m.adj_col[e], __ldg(m.adj_f + e) * d);
+    } else {
+        for (int e = begin; e < end; e += stride) atomic_add_field(cache + m.adj_col[e], m.adj_i[e] * dz);
+    }
+}
+
+// HUIO (Eq. energy_diff_upd): for every interaction term t containing s with
+// exponent e_s, and every other member k with exponent e_k,
+//   a_k^(e_k) += J_t ((z_s')^{e_s} - z_s^{e_s}) prod_{i in t \ {k, s}} z_i^{e_i}.
+template <class F, class Z>
+__device__ __forceinline__ void huio_update_range(const DevModel& m, const Z* zs, F* cache, int s, int begin,
+                                                  int end, int stride, long long z_old, long long z_new) {
+    for (int e = begin; e < end; e += stride) {
+        const int tt = m.inc_term[e];
+        const int es = m.inc_exp[e];
+        const int p0 = m.term_ptr[tt], p1 = m.term_ptr[tt + 1];
+        if constexpr (Num<F>::is_float) {
+            const float dpow = ipow<float>((float)z_new, es) - ipow<float>((float)z_old, es);
+            const float base = Coef<float>::tcoef(m, tt) * dpow;
+            for (int pk = p0; pk < p1; ++pk) {
+                const int k = m.mem_var[pk];
+                if (k == s) continue;
+                float prod = base;
+                for (int pi = p0; pi < p1; ++pi) {
+                    const int v = m.mem_var[pi];
+                    if (v == s || v == k) continue;
+                    prod *= ipow<float>((float)((long long)m.meta[v].lo + (long long)zs[v]), m.mem_exp[pi]);
+                }
+                const uint64_t om = m.omega[k];
+                const int ek = m.mem_exp[pk];
+                const int q = __popcll((om & ((1ull << ek) - 1ull)) >> 1);
+                atomic_add_field(cache + m.slot_base[k] + q, prod);
+            }
+        } else {
+            const long long dpow = ipow<long long>(z_new, es) - ipow<long long>(z_old, es);
+            const long long base = m.tcoef_i[tt] * dpow;
+            for (int pk = p0; pk < p1; ++pk) {
+                const int k = m.mem_var[pk];
+                if (k == s) continue;
+                long long prod = base;
+                for (int pi = p0; pi < p1; ++pi) {
+                    const int v = m.mem_var[pi];
+                    if (v == s || v == k) continue;
+                    prod *= ipow<long long>((long long)m.meta[v].lo + (long long)zs[v], m.mem_exp[pi]);
+                }
+                const uint64_t om = m.omega[k];
+                const int ek = m.mem_exp[pk];
+                const int q = __popcll((om & ((1ull << ek) - 1ull)) >> 1);
+                atomic_add_field(cache + m.slot_base[k] + q, prod);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ reductions
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the replica's threads; result valid in every thread.
+template <class T>
+__device__ T group_sum(T v, T* red, int t, int tpr, int bar_id) {
+    v = warp_sum(v);
+    const int w = t >> 5;
+    named_bar(bar_id, tpr);  // red[] free
+    if ((t & 31) == 0) red[w] = v;
+    named_bar(bar_id, tpr);
+    T tot = T(0);
+    for (int i = 0; i < (tpr >> 5); ++i) tot += red[i];
+    return tot;
+}
+
+// ------------------------------------------------------------------ the kernel
+template <class F, class Z, int RULE, int KIND, bool SMEM>
+__global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepArgs a) {
+    using Acc = typename Num<F>::Acc;
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    const DevModel& m = a.m;
+    const int slot = threadIdx.x / a.tpr;
+    const int t = threadIdx.x - slot * a.tpr;
+    const int r = blockIdx.x * a.rpc + slot;
+    if (slot >= a.rpc || r >= a.R) return;
+    const int bar_id = 1 + slot;
+    const int tpr = a.tpr;
+
+    uint8_t* base = SMEM ? (smem_raw + (size_t)slot * (size_t)a.rep_bytes) : (a.gstate + (size_t)r * (size_t)a.rep_bytes);
+    Z* zs = reinterpret_cast<Z*>(base + a.off_z);
+    F* cache = reinterpret_cast<F*>(base + a.off_cache);
+    int* ctl = reinterpret_cast<int*>(base + a.off_ctl);      // [3] list counters
+    int* list = reinterpret_cast<int*>(base + a.off_list);    // [cap][3]: var, z_old, z_new
+    Acc* red = reinterpret_cast<Acc*>(base + a.off_red);
+
+    // ---- random initial state (Sect. 3.1), or the caller's
+    for (int k = t; k < m.n; k += tpr) {
+        const VarMeta mt = m.meta[k];
+        uint32_t off;
+        if (a.init_states) {
+            off = (uint32_t)((long long)a.init_states[(size_t)r * m.n + k] - (long long)mt.lo);
+        } else {
+            const Words4 x = philox4x32_10((uint32_t)k, 0xFFFFFFFFu, (uint32_t)r, a.inst, a.key0, a.key1);
+            off = pick_below(x.x0, mt.width + 1u);
+        }
+        zs[k] = (Z)off;
+    }
+    if (t == 0) { ctl[0] = 0; ctl[1] = 0; ctl[2] = 0; }
+    named_bar(bar_id, tpr);
+
+    float drift = 0.f;
+    Acc e1 = 0, e2 = 0;
+    if constexpr (KIND == KIND_QUIO) quio_recompute<F, Z>(m, zs, cache, t, tpr, false, drift, e1, e2);
+    else huio_recompute<F, Z>(m, zs, cache, t, tpr, false, drift, e1, e2);
+    // per-thread energy accumulator: this thread's share of E(z_init)
+    Acc eacc;
+    if constexpr (KIND == KIND_QUIO) {
+        // pair share is counted twice over the replica; halve after the sum
+        Acc pair2 = group_sum<Acc>(e2, red, t, tpr, bar_id);
+        eacc = e1 + (t == 0 ? pair2 / 2 : Acc(0));
+    } else {
+        eacc = e1 + e2;
+        named_bar(bar_id, tpr);
+    }
+    if (t == 0) {
+        if constexpr (Num<F>::is_float) eacc += m.const_d;
+        else eacc += m.const_i;
+    }
+
+    unsigned long long changes = 0;
+    long long gl = 0;  // global level counter (parity of list counters)
+
+    for (int s = 0; s < a.S; ++s) {
+        const float beta = __ldg(a.beta + s);
+        const float ratio = __ldg(a.ratio + s);
+        for (int L = 0; L < m.n_levels; ++L, ++gl) {
+            int* cnt_now = ctl + (int)(gl % 3);
+            if (t == 0) ctl[(int)((gl + 1) % 3)] = 0;
+            const int lb = __ldg(m.lvl_ptr + L), le = __ldg(m.lvl_ptr + L + 1);
+            for (int i = lb + t; i < le; i += tpr) {
+                const int k = __ldg(m.lvl_vars + i);
+                const VarMeta mt = m.meta[k];
+                const long long lo = mt.lo;
+                const long long zo = (long long)zs[k];
+                const long long z = lo + zo;
+                long long v = z;
+                F de = F(0);
+                if (mt.width != 0) {
+                    const Words4 x = philox4x32_10((uint32_t)k, (uint32_t)s, (uint32_t)r, a.inst, a.key0, a.key1);
+                    VarView<F, KIND> vv;
+                    if constexpr (KIND == KIND_QUIO) {
+                        vv.f = cache[k];
+                        vv.d = Coef<F>::diag(m, k);
+                    } else {
+                        vv.a = cache + m.slot_base[k];
+                        vv.omega = m.omega[k];
+                    }
+                    const long long hi = lo + (long long)mt.width;
+                    if constexpr (RULE == RULE_HEAT_BATH) {
+                        if (vv.linear()) v = heat_bath_linear(Num<F>::to_f(vv.lin_coef()), lo, mt.width, x.x0, beta);
+                        else v = heat_bath_general<F, KIND>(vv, z, lo, mt.width, x.x0, beta);
+                        if (v != z) de = vv.delta(z, v);
+                    } else {
+                        long long prop;
+                        if (RULE == RULE_OPT && unit_open_right(x.x2) < ratio) {
+                            prop = opt_argmin<F, KIND>(vv, z, lo, hi);
+                        } else {
+                            const uint32_t j = pick_below(x.x0, mt.width);
+                            prop = lo + (long long)(j >= (uint32_t)zo ? j + 1u : j);
+                        }
+                        const F dprop = vv.delta(z, prop);
+                        if (metropolis_accept<F>(dprop, x.x1, beta)) {
+                            v = prop;
+                            de = dprop;
+                        }
+                    }
+                }
+                if (v != z) {
+                    zs[k] = (Z)(v - lo);
+                    eacc += (Acc)de;
+                    ++changes;
+                    const int len = mt.link_len;
+                    bool inline_upd = len <= a.heavy_links;
+                    if (!inline_upd) {
+                        const int idx = atomicAdd(cnt_now, 1);
+                        if (idx < a.list_cap) {
+                            list[3 * idx + 0] = k;
+                            list[3 * idx + 1] = (int)z;
+                            list[3 * idx + 2] = (int)v;
+                        } else {
+                            inline_upd = true;
+                        }
+                    }
+                    if (inline_upd) {
+                        if constexpr (KIND == KIND_QUIO)
+                            quio_update_range<F>(m, cache, mt.link_begin, mt.link_begin + len, 1, v - z);
+                        else
+                            huio_update_range<F, Z>(m, zs, cache, k, mt.link_begin, mt.link_begin + len, 1, z, v);
+                    }
+                }
+                if (a.trace != nullptr && r < a.trace_R)
+                    a.trace[((size_t)s * a.trace_R + r) * m.n + k] = (int32_t)v;
+            }
+            named_bar(bar_id, tpr);
+            const int cnt = *cnt_now;
+            if (cnt > 0) {
+                const int nl = cnt < a.list_cap ? cnt : a.list_cap;
+                for (int h = 0; h < nl; ++h) {
+                    const int k = list[3 * h + 0];
+                    const long long zold = list[3 * h + 1], znew = list[3 * h + 2];
+                    const VarMeta mt = m.meta[k];
+                    if constexpr (KIND == KIND_QUIO)
+                        quio_update_range<F>(m, cache, mt.link_begin + t, mt.link_begin + mt.link_len, tpr, znew - zold);
+                    else
+                        huio_update_range<F, Z>(m, zs, cache, k, mt.link_begin + t, mt.link_begin + mt.link_len, tpr,
+                                                zold, znew);
+                }
+                named_bar(bar_id, tpr);
+            }
+        }
+        // ---- FP64 refresh of float fields and energy
+        if constexpr (Num<F>::is_float) {
+            const bool last = (s + 1 == a.S);
+            if (last || (a.refresh_interval > 0 && (s + 1) % a.refresh_interval == 0)) {
+                Acc f1 = 0, f2 = 0;
+                if constexpr (KIND == KIND_QUIO) {
+                    quio_recompute<F, Z>(m, zs, cache, t, tpr, true, drift, f1, f2);
+                    Acc pair2 = group_sum<Acc>(f2, red, t, tpr, bar_id);
+                    eacc = f1 + (t == 0 ? pair2 / 2 : Acc(0));
+                } else {
+                    huio_recompute<F, Z>(m, zs, cache, t, tpr, true, drift, f1, f2);
+                    eacc = f1 + f2;
+                    named_bar(bar_id, tpr);
+                }
+                if (t == 0) eacc += m.const_d;
+            }
+        }
+        if (a.energy_trace != nullptr) {
+            const Acc tot = group_sum<Acc>(eacc, red, t, tpr, bar_id);
+            if (t == 0) reinterpret_cast<Acc*>(a.energy_trace)[(size_t)s * a.R + r] = tot;
+        }
+    }
+
+    // ---- outputs
+    const Acc etot = group_sum<Acc>(eacc, red, t, tpr, bar_id);
+    const unsigned long long ctot = group_sum<unsigned long long>(changes, reinterpret_cast<unsigned long long*>(red), t, tpr, bar_id);
+    for (int k = t; k < m.n; k += tpr)
+        a.out_states[(size_t)r * m.n + k] = (int32_t)((long long)m.meta[k].lo + (long long)zs[k]);
+    if (t == 0) {
+        reinterpret_cast<Acc*>(a.out_energies)[r] = etot;
+        if (a.out_accepts) a.out_accepts[r] = ctot;
+    }
+    if constexpr (Num<F>::is_float) {
+        if (a.drift_bits != nullptr) {
+            float dmax = drift;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+            if ((t & 31) == 0) atomicMax(a.drift_bits, __float_as_uint(dmax));
+        }
+    }
+}
+
+}  // namespace dev
+}  // namespace sa

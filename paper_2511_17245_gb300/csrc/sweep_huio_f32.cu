@@ -1,0 +1,9 @@
+// sweep_huio_f32.cu -- sweep kernels for HUIO models with f32 fields.
+#include "sweep_launch.cuh"
+
+namespace sa {
+int launch_sweep_huio_f32(const SweepArgs& a, int zbytes, int rule, bool smem, int blocks, int threads,
+                              size_t sh, void* stream) {
+    return launch_family<float, KIND_HUIO>(a, zbytes, rule, smem, blocks, threads, sh, (cudaStream_t)stream);
+}
+}  // namespace sa

@@ -1,0 +1,42 @@
+// sweep_launch.cuh -- instantiates the sweep kernel for one (field type,
+// model kind) pair over z width, rule and state placement.
+#pragma once
+
+#include "sweep.cuh"
+
+namespace sa {
+
+template <class F, class Z, int RULE, int KIND, bool SMEM>
+static int launch_one(const SweepArgs& a, int blocks, int threads, size_t shared_bytes, cudaStream_t st) {
+    auto kern = dev::sweep_kernel<F, Z, RULE, KIND, SMEM>;
+    if (shared_bytes > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shared_bytes);
+        if (e != cudaSuccess) return (int)e;
+    }
+    kern<<<blocks, threads, shared_bytes, st>>>(a);
+    return (int)cudaGetLastError();
+}
+
+template <class F, class Z, int KIND, bool SMEM>
+static int launch_rule(const SweepArgs& a, int rule, int blocks, int threads, size_t sh, cudaStream_t st) {
+    switch (rule) {
+    case RULE_METROPOLIS: return launch_one<F, Z, RULE_METROPOLIS, KIND, SMEM>(a, blocks, threads, sh, st);
+    case RULE_HEAT_BATH: return launch_one<F, Z, RULE_HEAT_BATH, KIND, SMEM>(a, blocks, threads, sh, st);
+    default: return launch_one<F, Z, RULE_OPT, KIND, SMEM>(a, blocks, threads, sh, st);
+    }
+}
+
+template <class F, int KIND>
+static int launch_family(const SweepArgs& a, int zbytes, int rule, bool smem, int blocks, int threads,
+                         size_t sh, cudaStream_t st) {
+    if (smem) {
+        if (zbytes == 1) return launch_rule<F, uint8_t, KIND, true>(a, rule, blocks, threads, sh, st);
+        if (zbytes == 2) return launch_rule<F, uint16_t, KIND, true>(a, rule, blocks, threads, sh, st);
+        return launch_rule<F, uint32_t, KIND, true>(a, rule, blocks, threads, sh, st);
+    }
+    if (zbytes == 1) return launch_rule<F, uint8_t, KIND, false>(a, rule, blocks, threads, sh, st);
+    if (zbytes == 2) return launch_rule<F, uint16_t, KIND, false>(a, rule, blocks, threads, sh, st);
+    return launch_rule<F, uint32_t, KIND, false>(a, rule, blocks, threads, sh, st);
+}
+
+}  // namespace sa

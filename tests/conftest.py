@@ -25,3 +25,12 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _built_libraries():
+    """Compile the CUDA library (sm_103a) and the oracle if they are stale."""
+    from paper_2511_17245_gb300 import build as b
+    from oracle import oracle as o
+    b.build()
+    o.build()
