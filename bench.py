@@ -1,0 +1,338 @@
+"""Benchmark: variable-update attempts/s of direct SA on one GB300.
+
+Workload (sparse float QUIO, wide range): N = 10,000 integer variables in
+[0, 255]; random graph with 80,000 edges (mean degree 16), J_ij, h_i ~ N(0,1)
+fp32, J_ii ~ U[0,1]; 1024 replicas; 1000 sweeps; geometric schedule between
+the model-derived temperatures of Sect. 3.4; FP32 fields with an FP64 refresh
+every 50 sweeps.  One step = one full run of each of the three rules
+(Metropolis, heat bath, optimal-transition Metropolis).  attempts = N R S per
+run.  Synthetic, seeded input (there is no dataset in the paper).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs the same
+workload on its own GPU (replicas only: no collective on the data path) and
+`value` is the sum of the ranks' attempts over the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_VARS, N_EDGES, LO, HI = 10_000, 80_000, 0, 255
+REPLICAS, SWEEPS, REFRESH = 1024, 1000, 50
+RULES = ["metropolis", "heat_bath", "opt_metropolis"]
+WORKLOAD = "quio_sparse_wide"
+METRIC = "variable-update attempts/s"
+UNIT = "attempts/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _config(extra=None):
+    c = {"workload": WORKLOAD, "n_vars": N_VARS, "n_edges": N_EDGES, "range": [LO, HI],
+         "replicas": REPLICAS, "sweeps": SWEEPS, "refresh_interval": REFRESH, "rules": RULES,
+         "coefficients": "fp32", "l2": "flushed between steps (512 MiB write)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle leg
+def oracle_sample(inst, replicas_per_rule=64, sweeps=2, threads=None):
+    """Times the oracle as it stands on the host cores: for each rule,
+    `replicas_per_rule` replicas of `sweeps` sweeps of the full-size model,
+    replicas spread over host threads.  Returns attempts/s over the three
+    rules (equal attempts per rule, as in the GPU step)."""
+    import concurrent.futures as cf
+    from oracle import oracle as orc
+    om = orc.Model(inst)
+    tmax, tmin = om.auto_temperatures()
+    threads = threads or os.cpu_count() or 1
+    total_t = 0.0
+    attempts = 0
+    per_rule = {}
+    for rule in RULES:
+        t0 = time.perf_counter()
+        with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+            list(ex.map(lambda r: om.run(rule, sweeps, 0, tmax, tmin, r_begin=r, r_end=r + 1),
+                        range(replicas_per_rule)))
+        dt = time.perf_counter() - t0
+        total_t += dt
+        a = N_VARS * replicas_per_rule * sweeps
+        attempts += a
+        per_rule[rule] = a / dt
+    return {"value": attempts / total_t, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{replicas_per_rule} replicas x {sweeps} sweeps of the full-size model per rule "
+                      f"(schedule over {sweeps} sweeps), threads over replicas",
+            "per_rule": per_rule, "seconds": total_t}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2511_17245_gb300 import workloads as wl
+    from oracle import oracle as orc
+    orc.build()
+    inst = wl.quio_sparse_wide(1, n=N_VARS, n_edges=N_EDGES, lo=LO, hi=HI)
+    for _ in range(args.warmup):
+        oracle_sample(inst, replicas_per_rule=16, sweeps=1)
+    times, vals = [], []
+    res = None
+    for _ in range(args.steps):
+        res = oracle_sample(inst, replicas_per_rule=args.ref_replicas, sweeps=1)
+        vals.append(res["value"])
+        times.append(res["seconds"])
+    value = float(np.median(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * float(np.mean(times)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
+            "data": "synthetic", "config": _config({"sample": res["sample"]}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": res["cores"],
+                             "sample": res["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU leg
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--ref-replicas", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rules", default=",".join(RULES))
+    ap.add_argument("--sweeps", type=int, default=SWEEPS,
+                    help="override for profiling a smaller case (bench numbers use the default)")
+    ap.add_argument("--replicas", type=int, default=REPLICAS,
+                    help="override for profiling a smaller case (bench numbers use the default)")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2511_17245_gb300 import Model, make_params, sa_model_create, sa_model_destroy, sa_run
+    from paper_2511_17245_gb300 import build as pkg_build
+    from paper_2511_17245_gb300 import workloads as wl
+    pkg_build.build()
+    rules = args.rules.split(",")
+
+    inst = wl.quio_sparse_wide(1, n=N_VARS, n_edges=N_EDGES, lo=LO, hi=HI)
+    model = Model(inst)
+    tmax, tmin = model.default_temperatures()
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    R, S, n = args.replicas, args.sweeps, N_VARS
+    states = torch.empty((R, n), dtype=torch.int32, device="cuda")
+    energies = torch.empty(R, dtype=torch.float64, device="cuda")
+    accepts = torch.empty(R, dtype=torch.int64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    params = {rule: make_params(rule, S, R, seed=rank, t_max=tmax, t_min=tmin, refresh_interval=REFRESH)
+              for rule in rules}
+
+    def one_step(record=None):
+        for rule in rules:
+            if record is not None:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            sa_run(model.handle, params[rule], states, energies, accepts, sptr)
+            if record is not None:
+                e1.record(stream)
+                record.append((rule, e0, e1))
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+
+    # ---- timed region (device time; L2 flushed between steps, outside the events)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    recs = []
+    step_events = []
+    acc_sum = 0
+    for _ in range(args.steps):
+        flush.zero_()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        one_step(recs)
+        s1.record(stream)
+        step_events.append((s0, s1))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in step_events]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    attempts_per_run = n * R * S
+    attempts = attempts_per_run * len(rules) * args.steps * world
+    value = attempts / (total_ms / 1000.0)
+    per_rule = {}
+    for rule in rules:
+        ms = [a.elapsed_time(b) for (rr, a, b) in recs if rr == rule]
+        per_rule[rule] = {"ms": float(np.mean(ms)), "attempts_per_s": attempts_per_run / (np.mean(ms) / 1000)}
+    acc_rate = float(accepts.double().mean().item()) / (n * S)
+
+    # ---- roofline of the dominant kernel (longest rule launch)
+    peaks, peak_kind = _peaks()
+    dom = max(per_rule, key=lambda r: per_rule[r]["ms"])
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    roof = None
+    if dom == "heat_bath":
+        # algorithmic: one exp per candidate value (u - l + 1 = 256) per attempt;
+        # peak: SFU exp2 at 16 results / clock / SM x 152 SMs x max SM clock
+        work = attempts_per_run * (HI - LO + 1)
+        achieved = work / (per_rule[dom]["ms"] / 1000.0) / 1e12
+        peak = 16 * 152 * sm_max * 1e6 / 1e12
+        roof = {"bound": "alu", "kernel": f"sweep_kernel<{dom}>", "achieved": achieved, "peak": peak,
+                "unit": "Texp/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": f"SFU 16/clk/SM x 152 SMs x {sm_max:.0f} MHz ({peak_kind} clock)"}
+    else:
+        # algorithmic bytes per attempt: read z_k (1 B) + f_k (4 B); on a change
+        # write z_k (1 B) and read-modify-write deg fields (8 B each) plus the
+        # CSR row (8 B per entry) shared by the replicas of a block
+        deg = 2 * N_EDGES / N_VARS
+        bpa = 5 + acc_rate * (1 + 8 * deg)
+        achieved = attempts_per_run * bpa / (per_rule[dom]["ms"] / 1000.0) / 1e9
+        peak = float(peaks["hbm_gbs"])
+        roof = {"bound": "hbm", "kernel": f"sweep_kernel<{dom}>", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": f"hbm_gbs ({peak_kind})"}
+
+    # ---- e2e through the C ABI with host buffers (model upload + host outputs each step)
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        hs = torch.empty((R, n), dtype=torch.int32).pin_memory()
+        he = torch.empty(R, dtype=torch.float64).pin_memory()
+        ha = torch.empty(R, dtype=torch.int64).pin_memory()
+        h2d = d2h = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(max(1, min(args.steps, 2))):
+            h = sa_model_create(inst["n_vars"], inst["lower"], inst["upper"], inst["term_offsets"],
+                                inst["term_vars"], inst["coeffs"], inst["coef_type"])
+            from paper_2511_17245_gb300 import sa_model_get_info
+            h2d += sa_model_get_info(h)["device_bytes"]
+            for rule in rules:
+                sa_run(h, params[rule], hs, he, ha, sptr)
+                d2h += hs.numel() * 4 + he.numel() * 8 + ha.numel() * 8
+            sa_model_destroy(h)
+        torch.cuda.synchronize()
+        reps = max(1, min(args.steps, 2))
+        dt = time.perf_counter() - t0
+        e2e = {"value": attempts_per_run * len(rules) * reps / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d / reps), "d2h_bytes_per_step": int(d2h / reps)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(inst, replicas_per_rule=args.ref_replicas, sweeps=1)
+        cpu.pop("seconds", None)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 refresh)", "data": "synthetic",
+                "config": _config({"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                                   "replicas": R, "sweeps": S}),
+                "per_rule": per_rule, "accept_rate_last_rule": acc_rate,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": len(rules) * args.steps, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -71,7 +71,12 @@ template <>
 struct Num<long long> {
     using Acc = long long;                 // energy accumulator
     static constexpr bool is_float = false;
-    __device__ static float to_f(long long v) { return __ll2float_rn(v); }
+    // int64 -> fp32, round to nearest.  On sm_103a the 64-bit conversion runs on
+    // the FP64 pipe; values that fit int32 take the 32-bit conversion, which
+    // rounds identically.
+    __device__ static float to_f(long long v) {
+        return (v == (long long)(int)v) ? __int2float_rn((int)v) : __ll2float_rn(v);
+    }
 };
 template <>
 struct Num<float> {
@@ -129,8 +134,8 @@ __device__ __forceinline__ T ipow(T x, int e) {
 template <class F>
 __device__ __forceinline__ F quio_delta(F f, F d, long long z, long long v) {
     if constexpr (Num<F>::is_float) {
-        const float dz = (float)(v - z);
-        return dz * fmaf(d, (float)(v + z), f);
+        const float vf = __int2float_rn((int)v), zf = __int2float_rn((int)z);
+        return (vf - zf) * fmaf(d, vf + zf, f);
     } else {
         return (v - z) * (f + d * (v + z));
     }
@@ -142,7 +147,7 @@ __device__ __forceinline__ F huio_delta(const F* a_slots, uint64_t omega, long l
     F acc = F(0);
     if constexpr (Num<F>::is_float) {
         float pv = 1.f, pz = 1.f;
-        const float vf = (float)v, zf = (float)z;
+        const float vf = __int2float_rn((int)v), zf = __int2float_rn((int)z);
         int slot = 0;
         uint64_t msk = omega >> 1;
         while (msk) {
@@ -186,6 +191,8 @@ template <class F>
 struct VarView<F, KIND_QUIO> {
     F f, d;
     __device__ F delta(long long z, long long v) const { return quio_delta<F>(f, d, z, v); }
+    // float models: candidate and current value already as floats
+    __device__ float delta_ff(float zf, float vf) const { return (vf - zf) * fmaf((float)d, vf + zf, (float)f); }
     __device__ bool linear() const { return d == F(0); }
     __device__ F lin_coef() const { return f; }
     __device__ int max_exp() const { return d == F(0) ? 1 : 2; }
@@ -197,6 +204,18 @@ struct VarView<F, KIND_HUIO> {
     const F* a;
     uint64_t omega;
     __device__ F delta(long long z, long long v) const { return huio_delta<F>(a, omega, z, v); }
+    __device__ float delta_ff(float zf, float vf) const {
+        float acc = 0.f, pv = 1.f, pz = 1.f;
+        int slot = 0;
+        uint64_t msk = omega >> 1;
+        while (msk) {
+            pv *= vf;
+            pz *= zf;
+            if (msk & 1ull) acc = fmaf((float)a[slot++], pv - pz, acc);
+            msk >>= 1;
+        }
+        return acc;
+    }
     __device__ bool linear() const { return (omega & ~2ull) == 0; }
     __device__ F lin_coef() const { return (omega & 2ull) ? a[0] : F(0); }
     __device__ int max_exp() const { return omega ? 63 - __clzll(omega) : 0; }
@@ -299,42 +318,147 @@ __device__ long long opt_argmin(const VarView<F, KIND>& vv, long long z, long lo
 }
 
 // ------------------------------------------------------------------ heat bath
-// Explicit inverse CDF over all u-l+1 values (Eq. prob_heatbath).  Three passes
-// over the candidates: minimum dE, compensated total, compensated search.
+__device__ __forceinline__ float ex2_ftz(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Explicit inverse CDF over all u-l+1 values (Eq. prob_heatbath).
+// Integer models: three passes over the candidates (minimum dE, compensated
+// total, compensated search) with fp32 weights expf(-fp32(dE_v - dE_min) beta),
+// the convention shared with the oracle.
+// Float models: the same three passes with the candidate value carried as an
+// exact float counter (no integer conversions in the loop) and weights
+// 2^((dE_min - dE_v) beta log2 e).
 template <class F, int KIND>
 __device__ long long heat_bath_general(const VarView<F, KIND>& vv, long long z, long long lo, uint32_t width,
                                        uint32_t xu, float beta) {
-    F mn = F(0);  // dE = 0 at the current value
-    for (uint32_t i = 0; i <= width; ++i) {
-        const F de = vv.delta(z, lo + (long long)i);
-        mn = de < mn ? de : mn;
+    if constexpr (Num<F>::is_float) {
+        const float zf = __int2float_rn((int)z), v0 = __int2float_rn((int)lo);
+        float mn = 0.f;
+        float vf = v0;
+        for (uint32_t i = 0; i <= width; ++i, vf += 1.f) mn = fminf(mn, vv.delta_ff(zf, vf));
+        const float b2 = beta * 1.4426950408889634f, mb = mn * b2;
+        float sum = 0.f, comp = 0.f;
+        vf = v0;
+        for (uint32_t i = 0; i <= width; ++i, vf += 1.f) {
+            const float w = ex2_ftz(fmaf(-vv.delta_ff(zf, vf), b2, mb));
+            const float y = w - comp;
+            const float t = sum + y;
+            comp = (t - sum) - y;
+            sum = t;
+        }
+        const float thr = unit_open_left(xu) * sum;
+        float run = 0.f, c2 = 0.f;
+        vf = v0;
+        for (uint32_t i = 0; i <= width; ++i, vf += 1.f) {
+            const float w = ex2_ftz(fmaf(-vv.delta_ff(zf, vf), b2, mb));
+            const float y = w - c2;
+            const float t = run + y;
+            c2 = (t - run) - y;
+            run = t;
+            if (run >= thr) return lo + (long long)i;
+        }
+        return lo + (long long)width;
+    } else {
+        F mn = F(0);  // dE = 0 at the current value
+        for (uint32_t i = 0; i <= width; ++i) {
+            const F de = vv.delta(z, lo + (long long)i);
+            mn = de < mn ? de : mn;
+        }
+        float sum = 0.f, comp = 0.f;
+        for (uint32_t i = 0; i <= width; ++i) {
+            const F de = vv.delta(z, lo + (long long)i);
+            const float w = expf(-(Num<F>::to_f(de - mn) * beta));
+            const float y = w - comp;
+            const float t = sum + y;
+            comp = (t - sum) - y;
+            sum = t;
+        }
+        const float thr = unit_open_left(xu) * sum;
+        float run = 0.f, c2 = 0.f;
+        for (uint32_t i = 0; i <= width; ++i) {
+            const F de = vv.delta(z, lo + (long long)i);
+            const float w = expf(-(Num<F>::to_f(de - mn) * beta));
+            const float y = w - c2;
+            const float t = run + y;
+            c2 = (t - run) - y;
+            run = t;
+            if (run >= thr) return lo + (long long)i;
+        }
+        return lo + (long long)width;
     }
-    float sum = 0.f, comp = 0.f;
-    for (uint32_t i = 0; i <= width; ++i) {
-        const F de = vv.delta(z, lo + (long long)i);
-        const float w = expf(-(Num<F>::to_f(de - mn) * beta));
-        const float y = w - comp;
-        const float t = sum + y;
-        comp = (t - sum) - y;
-        sum = t;
+}
+
+// Float QUIO with at most 256 values: dE(dz) = dz (c1 + d dz), dz = v - z,
+// c1 = f + 2 d z.  The minimum comes from the endpoints, dz = 0 and the
+// integers around the vertex; the weights of 16 blocks of 16 candidates are
+// summed in registers; the pick scans the block sums and recomputes one block.
+__device__ __forceinline__ long long heat_bath_quio_f32_small(float f, float d, long long z, long long lo,
+                                                              uint32_t width, uint32_t xu, float beta) {
+    const int n = (int)width + 1;
+    const float zf = __int2float_rn((int)z);
+    const float dz0 = __int2float_rn((int)(lo - z));
+    const float c1 = fmaf(2.f * d, zf, f);
+    const float dzn = dz0 + (float)width;
+    float mn = 0.f;
+    mn = fminf(mn, dz0 * fmaf(d, dz0, c1));
+    mn = fminf(mn, dzn * fmaf(d, dzn, c1));
+    if (d > 0.f) {
+        float q = floorf(-c1 / (2.f * d));
+        q = fminf(fmaxf(q, dz0), dzn);
+        const float q1 = fminf(q + 1.f, dzn);
+        mn = fminf(mn, q * fmaf(d, q, c1));
+        mn = fminf(mn, q1 * fmaf(d, q1, c1));
     }
-    const float thr = unit_open_left(xu) * sum;
-    float run = 0.f, c2 = 0.f;
-    for (uint32_t i = 0; i <= width; ++i) {
-        const F de = vv.delta(z, lo + (long long)i);
-        const float w = expf(-(Num<F>::to_f(de - mn) * beta));
-        const float y = w - c2;
-        const float t = run + y;
-        c2 = (t - run) - y;
-        run = t;
-        if (run >= thr) return lo + (long long)i;
+    const float b2 = beta * 1.4426950408889634f, mb = mn * b2;
+    float bs[16];
+    float tot = 0.f;
+#pragma unroll
+    for (int b = 0; b < 16; ++b) {
+        float acc = 0.f;
+        if (b * 16 < n) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int idx = b * 16 + j;
+                const float dz = dz0 + (float)idx;
+                const float w = ex2_ftz(fmaf(-dz * fmaf(d, dz, c1), b2, mb));
+                acc += (idx < n) ? w : 0.f;
+            }
+        }
+        bs[b] = acc;
+        tot += acc;
     }
-    return lo + (long long)width;
+    const float thr = unit_open_left(xu) * tot;
+    float run = 0.f;
+    int sel = -1;
+#pragma unroll
+    for (int b = 0; b < 16; ++b) {
+        if (sel < 0) {
+            const float nxt = run + bs[b];
+            if (nxt >= thr && b * 16 < n) sel = b;
+            else run = nxt;
+        }
+    }
+    if (sel < 0) return lo + (long long)width;
+    const int last = min(sel * 16 + 15, n - 1);
+    for (int idx = sel * 16; idx <= last; ++idx) {
+        const float dz = dz0 + (float)idx;
+        run += ex2_ftz(fmaf(-dz * fmaf(d, dz, c1), b2, mb));
+        if (run >= thr) return lo + (long long)idx;
+    }
+    return lo + (long long)last;
 }
 
 // Multilinear variable, dE = a (v - z): P(i) proportional to exp(-lambda i) on
-// i = 0..n-1, lambda = a beta; inverse transform of Eq. inverse_prob, written
-// with expm1/log1p; the pick is i = ceil(X) - 1 with X solving P_sum = Uc.
+// i = 0..n-1, lambda = a beta; inverse transform of Eq. inverse_prob.  The pick
+// is i = ceil(X) - 1 where X solves P_sum(X - 1) = Uc:
+//   lambda > 0:  X = -log1p(Uc expm1(-lambda n)) / lambda
+//   lambda < 0:  X = n - Y,  Y = -log1p((1 - Uc) expm1(-mu n)) / mu,  mu = -lambda,
+//                so i = (n - 1) - floor(Y)
+// (the second keeps the distance from the top, Y, as the computed quantity so
+// that neither a cancellation nor the spacing of floats near n loses it).
 __device__ __forceinline__ long long heat_bath_linear(float a, long long lo, uint32_t width, uint32_t xu,
                                                       float beta) {
     const float U = unit_open_left(xu);
@@ -342,23 +466,26 @@ __device__ __forceinline__ long long heat_bath_linear(float a, long long lo, uin
     long long i;
     if (width < (1u << 24)) {
         const float n = (float)(width + 1u);
-        float X;
         if (lam == 0.f) {
-            X = U * n;
+            i = (long long)ceilf(U * n) - 1;
         } else if (lam > 0.f) {
-            X = -log1pf(U * expm1f(-lam * n)) / lam;
+            const float X = -log1pf(U * expm1f(-lam * n)) / lam;
+            i = (long long)ceilf(X) - 1;
         } else {
             const float mu = -lam;
-            X = n + logf(U + (1.f - U) * expf(-mu * n)) / mu;
+            const float Y = -log1pf((1.f - U) * expm1f(-mu * n)) / mu;
+            i = (long long)width - (long long)floorf(Y);
         }
-        i = (long long)ceilf(X) - 1;
     } else {
         const double n = (double)width + 1.0, Ud = (double)U, l = (double)lam;
-        double X;
-        if (l == 0.0) X = Ud * n;
-        else if (l > 0.0) X = -log1p(Ud * expm1(-l * n)) / l;
-        else X = n + log(Ud + (1.0 - Ud) * exp(l * n)) / (-l);
-        i = (long long)ceil(X) - 1;
+        if (l == 0.0) {
+            i = (long long)ceil(Ud * n) - 1;
+        } else if (l > 0.0) {
+            i = (long long)ceil(-log1p(Ud * expm1(-l * n)) / l) - 1;
+        } else {
+            const double Y = -log1p((1.0 - Ud) * expm1(l * n)) / (-l);
+            i = (long long)width - (long long)floor(Y);
+        }
     }
     if (i < 0) i = 0;
     if (i > (long long)width) i = (long long)width;
@@ -641,8 +768,18 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepArgs a) {
                     }
                     const long long hi = lo + (long long)mt.width;
                     if constexpr (RULE == RULE_HEAT_BATH) {
-                        if (vv.linear()) v = heat_bath_linear(Num<F>::to_f(vv.lin_coef()), lo, mt.width, x.x0, beta);
-                        else v = heat_bath_general<F, KIND>(vv, z, lo, mt.width, x.x0, beta);
+                        if (vv.linear()) {
+                            v = heat_bath_linear(Num<F>::to_f(vv.lin_coef()), lo, mt.width, x.x0, beta);
+                        } else {
+                            bool done = false;
+                            if constexpr (Num<F>::is_float && KIND == KIND_QUIO) {
+                                if (mt.width < 256u && lo > -(1 << 22) && hi < (1 << 22)) {
+                                    v = heat_bath_quio_f32_small((float)vv.f, (float)vv.d, z, lo, mt.width, x.x0, beta);
+                                    done = true;
+                                }
+                            }
+                            if (!done) v = heat_bath_general<F, KIND>(vv, z, lo, mt.width, x.x0, beta);
+                        }
                         if (v != z) de = vv.delta(z, v);
                     } else {
                         long long prop;
