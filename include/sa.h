@@ -203,6 +203,39 @@ sa_status sa_run(const sa_model* model, const sa_run_params* params, int32_t* ou
 sa_status sa_energy(const sa_model* model, const int32_t* states, int64_t n_states, void* energies,
                     void* stream);
 
+/*
+ * sa_run_noalloc -- the run of sa_run for callers that must not allocate
+ * device memory.  (The paper has no counterpart; this is a library service.)
+ *
+ * Who needs it: code embedded in a host framework that owns all device memory
+ * through its own arena and forbids any other allocation, and latency-critical
+ * callers that cannot afford an allocation (which can synchronise the device)
+ * on the request path.  sa_run allocates its scratch per call; this variant
+ * calls no cudaMalloc, cudaFree or allocating library routine.
+ *
+ * Arguments and results are those of sa_run, with these differences:
+ *   - out_states, out_energies, out_accepts and params->init_states must be
+ *     device pointers (SA_ERR_INVALID otherwise); params->report must be NULL.
+ *   - The run's scratch (the per-sweep temperature table, and the replicas'
+ *     state when it does not fit in shared memory) lives in one fixed device
+ *     array of SA_NOALLOC_SCRATCH_BYTES bytes compiled into the library; every
+ *     device that loads the library holds it until the process exits.  A run
+ *     needing more (n_sweeps above SA_NOALLOC_SCRATCH_BYTES / 8, or replica
+ *     state that must spill to global memory and does not fit beside the table)
+ *     fails with SA_ERR_UNSUPPORTED and a message naming the limit.
+ *   - Every call on a device shares that array and it keeps the previous call's
+ *     contents; the kernel writes every scratch byte it reads.  Calls whose
+ *     work overlaps on the GPU (other streams, or a new call before the last
+ *     one finished on another stream) race on the array and must be serialised
+ *     by the caller.
+ *   - The first call on each device looks up the array's device address (with
+ *     that device current) and caches it; make that first call before any
+ *     stream capture.
+ */
+#define SA_NOALLOC_SCRATCH_BYTES (4u << 20)
+sa_status sa_run_noalloc(const sa_model* model, const sa_run_params* params, int32_t* out_states,
+                         void* out_energies, uint64_t* out_accepts, void* stream);
+
 /* Message of the last failed call on the calling thread ("" if none). */
 const char* sa_last_error(void);
 

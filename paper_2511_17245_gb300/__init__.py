@@ -9,10 +9,12 @@ from __future__ import annotations
 
 from . import _lib
 from ._lib import (RULES, SAError, make_params, sa_default_temperatures, sa_energy, sa_last_error,
-                   sa_model_create, sa_model_destroy, sa_model_get_info, sa_run, sa_run_report, sa_version)
+                   sa_model_create, sa_model_destroy, sa_model_get_info, sa_run, sa_run_noalloc, sa_run_report,
+                   sa_version)
 
 __all__ = ["Model", "RULES", "SAError", "make_params", "sa_default_temperatures", "sa_energy", "sa_last_error",
-           "sa_model_create", "sa_model_destroy", "sa_model_get_info", "sa_run", "sa_run_report", "sa_version"]
+           "sa_model_create", "sa_model_destroy", "sa_model_get_info", "sa_run", "sa_run_noalloc", "sa_run_report",
+           "sa_version"]
 
 
 class Model:

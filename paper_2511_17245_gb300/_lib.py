@@ -57,7 +57,9 @@ class sa_run_params(C.Structure):
 
 # Every symbol include/sa.h declares (checked by the tests).
 EXPORTS = ["sa_model_create", "sa_model_destroy", "sa_model_get_info", "sa_default_temperatures",
-           "sa_run", "sa_energy", "sa_last_error", "sa_version"]
+           "sa_run", "sa_energy", "sa_last_error", "sa_version", "sa_run_noalloc"]
+# size of the fixed device scratch array behind sa_run_noalloc (SA_NOALLOC_SCRATCH_BYTES)
+NOALLOC_SCRATCH_BYTES = 4 << 20
 
 
 def load():
@@ -81,6 +83,8 @@ def load():
         lib.sa_default_temperatures.restype = C.c_int
         lib.sa_run.argtypes = [P, C.POINTER(sa_run_params), P, P, P, P]
         lib.sa_run.restype = C.c_int
+        lib.sa_run_noalloc.argtypes = [P, C.POINTER(sa_run_params), P, P, P, P]
+        lib.sa_run_noalloc.restype = C.c_int
         lib.sa_energy.argtypes = [P, P, C.c_int64, P, P]
         lib.sa_energy.restype = C.c_int
         lib.sa_last_error.argtypes = []
@@ -177,6 +181,12 @@ def make_params(rule="metropolis", n_sweeps=1000, n_replicas=64, seed=0, t_max=0
 
 def sa_run(h, params: sa_run_params, out_states, out_energies, out_accepts=None, stream=None):
     _check(load().sa_run(h, C.byref(params), ptr(out_states), ptr(out_energies), ptr(out_accepts), stream))
+
+
+def sa_run_noalloc(h, params: sa_run_params, out_states, out_energies, out_accepts=None, stream=None):
+    """sa_run for callers that cannot allocate: device buffers only; the run's
+    scratch is the library's fixed device array (see include/sa.h)."""
+    _check(load().sa_run_noalloc(h, C.byref(params), ptr(out_states), ptr(out_energies), ptr(out_accepts), stream))
 
 
 def sa_energy(h, states, n_states, energies, stream=None):

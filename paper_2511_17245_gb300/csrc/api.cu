@@ -795,6 +795,25 @@ sa_status sa_energy(const sa_model* M, const int32_t* states, int64_t n_states, 
 
 const char* sa_last_error(void) { return g_last_error.c_str(); }
 
+// Internal view of a compiled model for other translation units of this library.
+__attribute__((visibility("hidden"))) int sa_internal_model_view(const sa_model* M, sa::ModelView* v) {
+    if (!M || !v) return 0;
+    v->dm = M->dm;
+    v->device = M->device;
+    v->n = M->n;
+    v->is_float = M->is_float ? 1 : 0;
+    v->max_exp = M->max_exp;
+    v->zbytes = M->zbytes;
+    v->cache_elems = M->cache_elems;
+    v->n_levels = M->n_levels;
+    v->de_max = M->de_max;
+    v->de_min = M->de_min;
+    return 1;
+}
+
+// Records a failure message for sa_last_error() from another translation unit.
+__attribute__((visibility("hidden"))) void sa_internal_set_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
 const char* sa_version(void) { return "paper_2511_17245_gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"

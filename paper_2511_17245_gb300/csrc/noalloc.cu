@@ -1,0 +1,196 @@
+// noalloc.cu -- sa_run_noalloc: the SA run of sa_run for callers that cannot
+// allocate device memory.
+//
+// Some callers are not allowed to call cudaMalloc/cudaFree (or anything that
+// allocates on their behalf): a host framework that owns all device memory
+// through its own arena and forbids other allocations, or a latency-critical
+// service where an allocation (which may synchronise the device) must not
+// happen on the request path.  This entry point serves them: the caller passes
+// device buffers for every input and output, and the run's own scratch (the
+// per-sweep temperature table and, when a replica's state does not fit on
+// chip, its state slab) lives in one fixed, file-scope device array of
+// SA_NOALLOC_SCRATCH_BYTES bytes that every device loading this library holds
+// until the process exits.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "sa.h"
+#include "sa_internal.h"
+
+extern "C" int sa_internal_model_view(const sa_model* M, sa::ModelView* v);
+extern "C" void sa_internal_set_error(const char* msg);
+
+namespace {
+
+// The shared scratch.  Every call on a device uses this same array and it
+// keeps whatever the last call left in it; calls whose work overlaps on the
+// GPU (two streams, or a second call before the first finished) race on it.
+static __device__ __align__(256) unsigned char g_scratch[SA_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void* g_scratch_ptr[kMaxDevices] = {nullptr};
+
+sa_status fail(sa_status st, const std::string& msg) {
+    sa_internal_set_error(msg.c_str());
+    return st;
+}
+
+// Device address of g_scratch on the current device.  In host code the name
+// g_scratch only denotes a host-side stand-in, so the address is looked up once
+// per device with that device current and cached.
+sa_status scratch_address(int dev, unsigned char** out) {
+    if (dev < 0 || dev >= kMaxDevices) return fail(SA_ERR_UNSUPPORTED, "device index beyond the scratch table");
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e != cudaSuccess) return fail(SA_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        g_scratch_ptr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_scratch_ptr[dev]);
+    return SA_OK;
+}
+
+bool on_device(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+extern "C" sa_status sa_run_noalloc(const sa_model* M, const sa_run_params* p, int32_t* out_states,
+                                    void* out_energies, uint64_t* out_accepts, void* stream) {
+    sa::ModelView mv;
+    if (!M || !p || !sa_internal_model_view(M, &mv)) return fail(SA_ERR_INVALID, "NULL model or params");
+    if (!out_states || !out_energies) return fail(SA_ERR_INVALID, "NULL output");
+    if (p->rule < 0 || p->rule > 2) return fail(SA_ERR_INVALID, "unknown rule");
+    if (p->n_sweeps < 1 || p->n_replicas < 1) return fail(SA_ERR_INVALID, "n_sweeps and n_replicas must be positive");
+    if (p->report) return fail(SA_ERR_INVALID, "sa_run_noalloc does not fill a report");
+    if (p->trace && (p->trace_replicas < 0 || p->trace_replicas > p->n_replicas))
+        return fail(SA_ERR_INVALID, "trace_replicas out of range");
+    if (p->rule == SA_OPT_METROPOLIS && mv.max_exp > 4)
+        return fail(SA_ERR_UNSUPPORTED, "optimal-transition Metropolis needs exponents <= 4");
+    if (!on_device(out_states) || !on_device(out_energies) || (out_accepts && !on_device(out_accepts)) ||
+        (p->init_states && !on_device(p->init_states)))
+        return fail(SA_ERR_INVALID, "sa_run_noalloc needs device buffers for every input and output");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != mv.device) return fail(SA_ERR_INVALID, "model belongs to another device");
+    unsigned char* scratch = nullptr;
+    sa_status st0 = scratch_address(dev, &scratch);
+    if (st0 != SA_OK) return st0;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int32_t S = p->n_sweeps, R = p->n_replicas, n = mv.n;
+
+    // temperature table: same arithmetic as sa_run (Sect. 3.1, Sect. 3.3.3)
+    const size_t tab_bytes = round_up(2 * (size_t)S * sizeof(float), 256);
+    if (tab_bytes > (size_t)SA_NOALLOC_SCRATCH_BYTES)
+        return fail(SA_ERR_UNSUPPORTED, "n_sweeps too large for the fixed scratch of sa_run_noalloc (limit " +
+                                            std::to_string(SA_NOALLOC_SCRATCH_BYTES / 8) + " sweeps)");
+    std::vector<float> tab(2 * (size_t)S);
+    double tmax = p->t_max, tmin = p->t_min;
+    if (!p->temperatures) {
+        if (tmax <= 0 && tmin <= 0) {
+            tmax = -mv.de_max / std::log(0.5);
+            tmin = -mv.de_min / std::log(0.001);
+        } else if (!(tmax > 0 && tmin > 0) || !std::isfinite(tmax) || !std::isfinite(tmin)) {
+            return fail(SA_ERR_INVALID, "t_max and t_min must both be positive (or both <= 0 for defaults)");
+        }
+    }
+    for (int32_t s = 0; s < S; ++s) {
+        double T;
+        if (p->temperatures) {
+            T = p->temperatures[s];
+            if (!(T > 0) || !std::isfinite(T)) return fail(SA_ERR_INVALID, "temperatures must be positive");
+        } else {
+            const double frac = S > 1 ? (double)s / (double)(S - 1) : 0.0;
+            T = tmax * std::pow(tmin / tmax, frac);
+        }
+        tab[s] = (float)(1.0 / T);
+        tab[S + s] = S > 1 ? (float)s / (float)(S - 1) : 0.0f;
+    }
+
+    // launch shape: the automatic choice of sa_run
+    const size_t fsize = mv.is_float ? 4 : 8;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int tpr = p->threads_per_replica;
+    if (tpr <= 0) {
+        const double mean_w = (double)n / (double)(mv.n_levels > 0 ? mv.n_levels : 1);
+        const int want = (int)std::ceil(mean_w / 2.0);
+        tpr = std::min(256, std::max(32, (want + 31) / 32 * 32));
+    }
+    if (tpr % 32 != 0 || tpr > 512) return fail(SA_ERR_INVALID, "threads_per_replica must be a multiple of 32, <= 512");
+    const int list_cap = 64;
+    const size_t off_z = 0;
+    const size_t off_cache = round_up(off_z + (size_t)n * mv.zbytes, 16);
+    const size_t off_ctl = round_up(off_cache + (size_t)mv.cache_elems * fsize, 16);
+    const size_t off_list = off_ctl + 16;
+    const size_t off_red = round_up(off_list + (size_t)list_cap * 12, 16);
+    const size_t rep_bytes = round_up(off_red + (size_t)(tpr / 32) * 8, 16);
+    int fit = (int)((size_t)sa::sweep_max_shared_optin() / rep_bytes);
+    fit = std::min(fit, std::min(15, 512 / tpr));
+    const bool in_global = (fit < 1) || (p->flags & SA_FLAG_STATE_IN_GLOBAL);
+    int rpc = p->replicas_per_block;
+    if (rpc <= 0) {
+        const int target = std::max(1, (R + sms - 1) / std::max(1, sms));
+        rpc = in_global ? std::min(target, std::min(15, 512 / tpr)) : std::min(fit, target);
+    }
+    if (rpc < 1 || rpc > 15 || rpc * tpr > 512) return fail(SA_ERR_INVALID, "replicas_per_block out of range");
+    if (!in_global && rpc > fit) return fail(SA_ERR_INVALID, "replicas_per_block exceeds shared memory");
+    const size_t slab_bytes = in_global ? (size_t)R * rep_bytes : 0;
+    if (tab_bytes + slab_bytes > (size_t)SA_NOALLOC_SCRATCH_BYTES)
+        return fail(SA_ERR_UNSUPPORTED, "replica state does not fit on chip and " + std::to_string(R) +
+                                            " replicas exceed the fixed scratch of sa_run_noalloc (" +
+                                            std::to_string(SA_NOALLOC_SCRATCH_BYTES) + " bytes)");
+    const int blocks = (R + rpc - 1) / rpc;
+    const size_t shared = in_global ? 0 : (size_t)rpc * rep_bytes;
+
+    float* d_tab = reinterpret_cast<float*>(scratch);
+    cudaError_t e = cudaMemcpyAsync(d_tab, tab.data(), 2 * (size_t)S * sizeof(float), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return fail(SA_ERR_CUDA, std::string("copy schedule: ") + cudaGetErrorString(e));
+
+    sa::SweepArgs a{};
+    a.m = mv.dm;
+    a.R = R;
+    a.S = S;
+    a.key0 = (uint32_t)(p->seed & 0xFFFFFFFFull);
+    a.key1 = (uint32_t)(p->seed >> 32);
+    a.inst = p->instance_id;
+    a.refresh_interval = p->refresh_interval > 0 ? p->refresh_interval : 50;
+    a.beta = d_tab;
+    a.ratio = d_tab + S;
+    a.init_states = p->init_states;
+    a.out_states = out_states;
+    a.out_energies = out_energies;
+    a.out_accepts = (unsigned long long*)out_accepts;
+    a.trace = p->trace;
+    a.trace_R = p->trace ? p->trace_replicas : 0;
+    a.energy_trace = p->energy_trace;
+    a.drift_bits = nullptr;
+    a.gstate = in_global ? scratch + tab_bytes : nullptr;   // every slab byte is written before it is read
+    a.rep_bytes = (int64_t)rep_bytes;
+    a.off_z = (int32_t)off_z;
+    a.off_cache = (int32_t)off_cache;
+    a.off_ctl = (int32_t)off_ctl;
+    a.off_list = (int32_t)off_list;
+    a.off_red = (int32_t)off_red;
+    a.rpc = rpc;
+    a.tpr = tpr;
+    a.heavy_links = 64;
+    a.list_cap = list_cap;
+    const int le = sa::launch_sweep(a, mv.zbytes, p->rule, !in_global, blocks, rpc * tpr, shared, stream);
+    if (le != 0) return fail(SA_ERR_CUDA, std::string("sweep launch: ") + cudaGetErrorString((cudaError_t)le));
+    return SA_OK;
+}

@@ -101,6 +101,19 @@ struct EnergyArgs {
     int32_t* bad;               // set to 1 if a value lies outside its bounds
 };
 
+// Read-only view of a compiled model for translation units other than api.cu.
+struct ModelView {
+    DevModel dm;
+    int device;
+    int32_t n;
+    int is_float;
+    int max_exp;
+    int zbytes;
+    int64_t cache_elems;
+    int32_t n_levels;
+    double de_max, de_min;
+};
+
 // Host-side launchers implemented in the .cu files.
 // zbytes in {1,2,4}; returns a cudaError_t as int.
 int launch_sweep(const SweepArgs& a, int zbytes, int rule, bool smem, int blocks, int threads,
