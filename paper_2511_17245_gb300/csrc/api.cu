@@ -309,7 +309,7 @@ sa_status compile_model(sa_model* M, int32_t n, const int64_t* lower, const int6
     dm.const_i = (int64_t)const_i;
     dm.const_d = const_d;
     struct Offs {
-        size_t meta, lvl_ptr, lvl_vars;
+        size_t meta, lvl_ptr, lvl_vars, lvl_rec;
         size_t adj_col, adj_i, adj_f, adj_d, lin_i, lin_f, lin_d, diag_i, diag_f, diag_d;
         size_t slot_base, omega, aconst_i, aconst_f, aconst_d, inc_term, inc_exp, term_ptr, mem_var, mem_exp,
             tcoef_i, tcoef_f, tcoef_d;
@@ -327,11 +327,13 @@ sa_status compile_model(sa_model* M, int32_t n, const int64_t* lower, const int6
                 deg[t.mem[1].var]++;
             }
         }
+        // rows padded to multiples of 4 entries (16-byte aligned starts for
+        // vector loads); padding entries are never read as entries
         std::vector<int64_t> ptr(n + 1, 0);
-        for (int32_t k = 0; k < n; ++k) ptr[k + 1] = ptr[k] + deg[k];
-        std::vector<int32_t> col(ptr[n]);
-        std::vector<int64_t> vi(ptr[n]);
-        std::vector<double> vd(ptr[n]);
+        for (int32_t k = 0; k < n; ++k) ptr[k + 1] = ptr[k] + (deg[k] + 3) / 4 * 4;
+        std::vector<int32_t> col(ptr[n], 0);
+        std::vector<int64_t> vi(ptr[n], 0);
+        std::vector<double> vd(ptr[n], 0.0);
         std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
         for (auto& t : terms) {
             if (t.mem.size() == 1) {
@@ -346,8 +348,7 @@ sa_status compile_model(sa_model* M, int32_t n, const int64_t* lower, const int6
         }
         // sort each row by column for locality
         for (int32_t k = 0; k < n; ++k) {
-            std::vector<std::pair<int32_t, int64_t>> rowi;
-            std::vector<int64_t> order(ptr[k + 1] - ptr[k]);
+            std::vector<int64_t> order(deg[k]);
             for (size_t i = 0; i < order.size(); ++i) order[i] = ptr[k] + (int64_t)i;
             std::sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return col[x] < col[y]; });
             std::vector<int32_t> c2(order.size());
@@ -358,16 +359,54 @@ sa_status compile_model(sa_model* M, int32_t n, const int64_t* lower, const int6
         }
         if (ptr[n] > INT32_MAX) return fail(SA_ERR_UNSUPPORTED, "more than 2^31 adjacency entries");
         for (int32_t k = 0; k < n; ++k) {
-            meta[k] = {lo[k], width[k], (int32_t)ptr[k], (int32_t)(ptr[k + 1] - ptr[k])};
+            meta[k] = {lo[k], width[k], (int32_t)ptr[k], (int32_t)deg[k]};
             M->max_link_len = std::max(M->max_link_len, meta[k].link_len);
         }
-        M->n_links = ptr[n];
-        nb_ptr = ptr;
-        nb = col;
+        M->n_links = 0;
+        for (int32_t k = 0; k < n; ++k) M->n_links += deg[k];
+        // neighbour lists for the levels (without padding)
+        nb_ptr.assign(n + 1, 0);
+        for (int32_t k = 0; k < n; ++k) nb_ptr[k + 1] = nb_ptr[k] + deg[k];
+        nb.resize(nb_ptr[n]);
+        for (int32_t k = 0; k < n; ++k)
+            for (int64_t i = 0; i < deg[k]; ++i) nb[nb_ptr[k] + i] = col[ptr[k] + i];
         build_levels(n, nb_ptr, nb, lvl_ptr, lvl_vars, M->n_levels);
+        // Variables of one level are independent, so their order inside the
+        // level is free.  Sorting by (J_kk, u_k - l_k) puts variables whose
+        // heat-bath windows have similar widths into the same warp.
+        for (int32_t L = 0; L < M->n_levels; ++L) {
+            auto b = lvl_vars.begin() + lvl_ptr[L], e = lvl_vars.begin() + lvl_ptr[L + 1];
+            std::stable_sort(b, e, [&](int32_t x, int32_t y) {
+                const double dx = M->is_float ? diag_d[x] : (double)diag_i[x];
+                const double dy = M->is_float ? diag_d[y] : (double)diag_i[y];
+                if (dx != dy) return dx > dy;
+                return width[x] > width[y];
+            });
+        }
+        std::vector<sa::LevelRec> rec(n);
+        for (int32_t i = 0; i < n; ++i) {
+            const int32_t k = lvl_vars[i];
+            sa::LevelRec& q = rec[i];
+            q.k = k;
+            q.lo = meta[k].lo;
+            q.width = meta[k].width;
+            q.link_begin = meta[k].link_begin;
+            q.link_len = meta[k].link_len;
+            q.slot_base = 0;
+            if (M->is_float) {
+                const float dv = (float)diag_d[k];
+                std::memcpy(&q.aux0, &dv, 4);
+                q.aux1 = 0;
+            } else {
+                const uint64_t dv = (uint64_t)diag_i[k];
+                q.aux0 = (uint32_t)dv;
+                q.aux1 = (uint32_t)(dv >> 32);
+            }
+        }
         off.meta = blob.add(meta);
         off.lvl_ptr = blob.add(lvl_ptr);
         off.lvl_vars = blob.add(lvl_vars);
+        off.lvl_rec = blob.add(rec);
         off.adj_col = blob.add(col);
         if (M->is_float) {
             std::vector<float> vf(vd.size()), lf(n), df(n);
@@ -451,9 +490,23 @@ sa_status compile_model(sa_model* M, int32_t n, const int64_t* lower, const int6
         }
         build_levels(n, nb_ptr, nb, lvl_ptr, lvl_vars, M->n_levels);
         slot_base.resize(n);
+        std::vector<sa::LevelRec> rec(n);
+        for (int32_t i = 0; i < n; ++i) {
+            const int32_t k = lvl_vars[i];
+            sa::LevelRec& q = rec[i];
+            q.k = k;
+            q.lo = meta[k].lo;
+            q.width = meta[k].width;
+            q.link_begin = meta[k].link_begin;
+            q.link_len = meta[k].link_len;
+            q.slot_base = slot_base[k];
+            q.aux0 = (uint32_t)omega[k];
+            q.aux1 = (uint32_t)(omega[k] >> 32);
+        }
         off.meta = blob.add(meta);
         off.lvl_ptr = blob.add(lvl_ptr);
         off.lvl_vars = blob.add(lvl_vars);
+        off.lvl_rec = blob.add(rec);
         off.slot_base = blob.add(slot_base);
         off.omega = blob.add(omega);
         off.inc_term = blob.add(inc_term);
@@ -486,6 +539,7 @@ sa_status compile_model(sa_model* M, int32_t n, const int64_t* lower, const int6
     dm.meta = at<VarMeta>(b, off.meta);
     dm.lvl_ptr = at<int32_t>(b, off.lvl_ptr);
     dm.lvl_vars = at<int32_t>(b, off.lvl_vars);
+    dm.lvl_rec = at<sa::LevelRec>(b, off.lvl_rec);
     if (dm.kind == sa::KIND_QUIO) {
         dm.adj_col = at<int32_t>(b, off.adj_col);
         if (M->is_float) {

@@ -17,6 +17,19 @@ struct VarMeta {
     int32_t link_len;     // number of adjacency / incidence entries
 };
 
+// Per-variable record in dependency-level order, 32 bytes, everything one
+// attempt needs besides the replica state.  aux holds J_kk (QUIO; fp32 bits or
+// int64) or the exponent mask Omega_k (HUIO).
+struct alignas(16) LevelRec {
+    int32_t k;
+    int32_t lo;
+    uint32_t width;
+    int32_t link_begin;
+    int32_t link_len;
+    int32_t slot_base;
+    uint32_t aux0, aux1;
+};
+
 // Device-resident compiled model.  All pointers are device pointers into one
 // allocation.  For integer models the *_i arrays are used; for float models
 // the *_f arrays drive the sweep and the *_d arrays the FP64 refresh.
@@ -28,6 +41,7 @@ struct DevModel {
     const VarMeta* meta;        // [n]
     const int32_t* lvl_ptr;     // [n_levels + 1]
     const int32_t* lvl_vars;    // [n]: variables grouped by dependency level
+    const LevelRec* lvl_rec;    // [n]: their records, same order
 
     // QUIO (every term of total degree <= 2):
     //   E = c + sum_k lin_k z_k + sum_k diag_k z_k^2 + sum_{i<j} J_ij z_i z_j

@@ -331,70 +331,179 @@ __device__ __forceinline__ float ex2_ftz(float x) {
 // Float models: the same three passes with the candidate value carried as an
 // exact float counter (no integer conversions in the loop) and weights
 // 2^((dE_min - dE_v) beta log2 e).
+// Weights below exp(-(20 + ln n)) times the largest one are left out of the
+// heat-bath sum: with n candidates their total is below e^-20 of the total,
+// far inside the near-threshold margin of the decision.  Candidates are
+// dropped only in whole blocks, and only when a lower bound of dE over the
+// block proves every weight in it small.
+__device__ __forceinline__ float hb_cut(uint32_t width) { return 20.f + logf((float)width + 1.f); }
+
+// Lower bound of dE over the candidate values [v0, v1] of a QUIO variable:
+// dE(v) = (v - z)(f + d (v + z)) is convex (d > 0) or concave (d <= 0) in v, so
+// the minimum over an interval is at an endpoint or next to the vertex
+// v* = -f / (2 d).
+template <class F>
+__device__ __forceinline__ F quio_interval_min(const VarView<F, KIND_QUIO>& vv, long long z, long long v0,
+                                               long long v1) {
+    F mnb = vv.delta(z, v0);
+    const F e1 = vv.delta(z, v1);
+    mnb = e1 < mnb ? e1 : mnb;
+    if (vv.d > F(0)) {
+        long long q;
+        if constexpr (Num<F>::is_float) {
+            float qv = floorf(-(float)vv.f / (2.f * (float)vv.d));
+            qv = fminf(fmaxf(qv, (float)v0), (float)v1);
+            q = (long long)qv;
+        } else {
+            q = floor_div(-vv.f, 2 * vv.d);
+        }
+        if (q >= v0 && q <= v1) { const F e = vv.delta(z, q); mnb = e < mnb ? e : mnb; }
+        if (q + 1 >= v0 && q + 1 <= v1) { const F e = vv.delta(z, q + 1); mnb = e < mnb ? e : mnb; }
+    }
+    return mnb;
+}
+
+// Explicit inverse CDF over all u-l+1 values (Eq. prob_heatbath).
+// Integer models: three passes over the candidates (minimum dE, compensated
+// total, compensated search) with fp32 weights expf(-fp32(dE_v - dE_min) beta),
+// the convention shared with the oracle.
+// Float models: the same three passes with the candidate value carried as an
+// exact float counter (no integer conversions in the loop) and weights
+// 2^((dE_min - dE_v) beta log2 e).
+// QUIO variables skip blocks of 32 values whose weights are all negligible
+// (see hb_cut); the minimum then comes from the interval bounds as well.
 template <class F, int KIND>
 __device__ long long heat_bath_general(const VarView<F, KIND>& vv, long long z, long long lo, uint32_t width,
                                        uint32_t xu, float beta) {
-    if constexpr (Num<F>::is_float) {
-        const float zf = __int2float_rn((int)z), v0 = __int2float_rn((int)lo);
-        float mn = 0.f;
-        float vf = v0;
-        for (uint32_t i = 0; i <= width; ++i, vf += 1.f) mn = fminf(mn, vv.delta_ff(zf, vf));
-        const float b2 = beta * 1.4426950408889634f, mb = mn * b2;
-        float sum = 0.f, comp = 0.f;
-        vf = v0;
-        for (uint32_t i = 0; i <= width; ++i, vf += 1.f) {
-            const float w = ex2_ftz(fmaf(-vv.delta_ff(zf, vf), b2, mb));
-            const float y = w - comp;
-            const float t = sum + y;
-            comp = (t - sum) - y;
-            sum = t;
-        }
-        const float thr = unit_open_left(xu) * sum;
-        float run = 0.f, c2 = 0.f;
-        vf = v0;
-        for (uint32_t i = 0; i <= width; ++i, vf += 1.f) {
-            const float w = ex2_ftz(fmaf(-vv.delta_ff(zf, vf), b2, mb));
-            const float y = w - c2;
-            const float t = run + y;
-            c2 = (t - run) - y;
-            run = t;
-            if (run >= thr) return lo + (long long)i;
-        }
-        return lo + (long long)width;
+    constexpr uint32_t B = 32;
+    const uint32_t nblk = width / B + 1;
+    // minimum over all values (current value included: dE = 0)
+    F mn = F(0);
+    if constexpr (KIND == KIND_QUIO) {
+        const F e = quio_interval_min<F>(vv, z, lo, lo + (long long)width);
+        mn = e < mn ? e : mn;
     } else {
-        F mn = F(0);  // dE = 0 at the current value
         for (uint32_t i = 0; i <= width; ++i) {
             const F de = vv.delta(z, lo + (long long)i);
             mn = de < mn ? de : mn;
         }
+    }
+    // kept window [wb0, wb1] of blocks: for a convex QUIO variable the block
+    // lower bound falls and then rises, so the first and last kept blocks are
+    // found by bisection on either side of the vertex; otherwise every block.
+    uint32_t wb0 = 0, wb1 = nblk - 1;
+    if constexpr (KIND == KIND_QUIO) {
+        if (vv.d > F(0)) {
+            const float cutv = hb_cut(width);
+            auto kept = [&](uint32_t b) -> bool {
+                const long long v0 = lo + (long long)(b * B);
+                const long long v1 = lo + (long long)min(width, b * B + (B - 1));
+                return Num<F>::to_f(quio_interval_min<F>(vv, z, v0, v1) - mn) * beta <= cutv;
+            };
+            // block holding the minimum
+            long long vstar;
+            if constexpr (Num<F>::is_float) {
+                float qv = floorf(-(float)vv.f / (2.f * (float)vv.d));
+                qv = fminf(fmaxf(qv, (float)lo), (float)(lo + (long long)width));
+                vstar = (long long)qv;
+            } else {
+                vstar = floor_div(-vv.f, 2 * vv.d);
+                if (vstar < lo) vstar = lo;
+                if (vstar > lo + (long long)width) vstar = lo + (long long)width;
+            }
+            uint32_t bm = (uint32_t)(vstar - lo) / B;
+            if (!kept(bm)) {  // rounding: fall back to every block
+                bm = 0;
+            } else {
+                uint32_t a = 0, c = bm;  // first kept block in [0, bm]
+                while (a < c) { const uint32_t mid = (a + c) / 2; if (kept(mid)) c = mid; else a = mid + 1; }
+                wb0 = a;
+                a = bm; c = nblk - 1;   // last kept block in [bm, nblk-1]
+                while (a < c) { const uint32_t mid = (a + c + 1) / 2; if (kept(mid)) a = mid; else c = mid - 1; }
+                wb1 = a;
+            }
+        }
+    }
+    if constexpr (Num<F>::is_float) {
+        const float zf = __int2float_rn((int)z), v0f = __int2float_rn((int)lo);
+        const float b2 = beta * 1.4426950408889634f, mb = (float)mn * b2;
         float sum = 0.f, comp = 0.f;
-        for (uint32_t i = 0; i <= width; ++i) {
-            const F de = vv.delta(z, lo + (long long)i);
-            const float w = expf(-(Num<F>::to_f(de - mn) * beta));
-            const float y = w - comp;
-            const float t = sum + y;
-            comp = (t - sum) - y;
-            sum = t;
+        for (uint32_t b = wb0; b <= wb1; ++b) {
+            const uint32_t e = min(width, b * B + (B - 1));
+            float vf = v0f + (float)(b * B);
+            for (uint32_t i = b * B; i <= e; ++i, vf += 1.f) {
+                const float w = ex2_ftz(fmaf(-vv.delta_ff(zf, vf), b2, mb));
+                const float y = w - comp;
+                const float t = sum + y;
+                comp = (t - sum) - y;
+                sum = t;
+            }
         }
         const float thr = unit_open_left(xu) * sum;
         float run = 0.f, c2 = 0.f;
-        for (uint32_t i = 0; i <= width; ++i) {
-            const F de = vv.delta(z, lo + (long long)i);
-            const float w = expf(-(Num<F>::to_f(de - mn) * beta));
-            const float y = w - c2;
-            const float t = run + y;
-            c2 = (t - run) - y;
-            run = t;
-            if (run >= thr) return lo + (long long)i;
+        long long last = lo;
+        for (uint32_t b = wb0; b <= wb1; ++b) {
+            const uint32_t e = min(width, b * B + (B - 1));
+            float vf = v0f + (float)(b * B);
+            for (uint32_t i = b * B; i <= e; ++i, vf += 1.f) {
+                const float w = ex2_ftz(fmaf(-vv.delta_ff(zf, vf), b2, mb));
+                const float y = w - c2;
+                const float t = run + y;
+                c2 = (t - run) - y;
+                run = t;
+                last = lo + (long long)i;
+                if (run >= thr) return last;
+            }
         }
-        return lo + (long long)width;
+        return last;
+    } else {
+        float sum = 0.f, comp = 0.f;
+        for (uint32_t b = wb0; b <= wb1; ++b) {
+            const uint32_t e = min(width, b * B + (B - 1));
+            for (uint32_t i = b * B; i <= e; ++i) {
+                const F de = vv.delta(z, lo + (long long)i);
+                const float w = expf(-(Num<F>::to_f(de - mn) * beta));
+                const float y = w - comp;
+                const float t = sum + y;
+                comp = (t - sum) - y;
+                sum = t;
+            }
+        }
+        const float thr = unit_open_left(xu) * sum;
+        float run = 0.f, c2 = 0.f;
+        long long last = lo;
+        for (uint32_t b = wb0; b <= wb1; ++b) {
+            const uint32_t e = min(width, b * B + (B - 1));
+            for (uint32_t i = b * B; i <= e; ++i) {
+                const F de = vv.delta(z, lo + (long long)i);
+                const float w = expf(-(Num<F>::to_f(de - mn) * beta));
+                const float y = w - c2;
+                const float t = run + y;
+                c2 = (t - run) - y;
+                run = t;
+                last = lo + (long long)i;
+                if (run >= thr) return last;
+            }
+        }
+        return last;
     }
 }
 
 // Float QUIO with at most 256 values: dE(dz) = dz (c1 + d dz), dz = v - z,
 // c1 = f + 2 d z.  The minimum comes from the endpoints, dz = 0 and the
-// integers around the vertex; the weights of 16 blocks of 16 candidates are
-// summed in registers; the pick scans the block sums and recomputes one block.
+// integers around the vertex.  The kept window is derived in closed form: for
+// d > 0 with the vertex vq inside the range every value with
+// dE - dE_min <= C (C = the cut times T) satisfies d (dz - vq)^2 <= C + d/4, so
+// vq -/+ sqrt(C/d + 1/4) brackets it; with the vertex outside the range dE is
+// monotone over it and, by convexity, the window ends within C / slope of the
+// minimising endpoint; for d <= 0 the window is the whole range.  Blocks of 16
+// values counted from the window start (so every lane loops over its own
+// window) are summed in registers; the pick scans the block sums and
+// recomputes one block.
+__device__ __forceinline__ float quio_w(float dz, float d, float c1, float b2, float mb) {
+    return ex2_ftz(fmaf(-dz * fmaf(d, dz, c1), b2, mb));
+}
+
 __device__ __forceinline__ long long heat_bath_quio_f32_small(float f, float d, long long z, long long lo,
                                                               uint32_t width, uint32_t xu, float beta) {
     const int n = (int)width + 1;
@@ -402,29 +511,45 @@ __device__ __forceinline__ long long heat_bath_quio_f32_small(float f, float d, 
     const float dz0 = __int2float_rn((int)(lo - z));
     const float c1 = fmaf(2.f * d, zf, f);
     const float dzn = dz0 + (float)width;
-    float mn = 0.f;
-    mn = fminf(mn, dz0 * fmaf(d, dz0, c1));
-    mn = fminf(mn, dzn * fmaf(d, dzn, c1));
+    const float e0 = dz0 * fmaf(d, dz0, c1), en = dzn * fmaf(d, dzn, c1);
+    float mn = fminf(0.f, fminf(e0, en));
+    const float C = hb_cut(width) / beta;
+    float wlo = dz0, whi = dzn;
     if (d > 0.f) {
-        float q = floorf(-c1 / (2.f * d));
-        q = fminf(fmaxf(q, dz0), dzn);
-        const float q1 = fminf(q + 1.f, dzn);
-        mn = fminf(mn, q * fmaf(d, q, c1));
-        mn = fminf(mn, q1 * fmaf(d, q1, c1));
+        const float vq = -c1 / (2.f * d);
+        if (vq > dz0 && vq < dzn) {
+            const float q = floorf(vq), q1 = q + 1.f;
+            mn = fminf(mn, fminf(q * fmaf(d, q, c1), q1 * fmaf(d, q1, c1)));
+            const float h = sqrtf(C / d + 0.25f) + 1.f;
+            wlo = fmaxf(dz0, floorf(vq - h));
+            whi = fminf(dzn, ceilf(vq + h));
+        } else if (vq <= dz0) {      // increasing over the range: minimum at dz0
+            const float slope = fmaf(d, fmaf(2.f, dz0, 1.f), c1);   // dE(dz0 + 1) - dE(dz0) > 0
+            whi = fminf(dzn, dz0 + ceilf(C / slope) + 1.f);
+        } else {                      // decreasing: minimum at dzn
+            const float slope = -fmaf(d, fmaf(2.f, dzn, -1.f), c1); // dE(dzn - 1) - dE(dzn) > 0
+            wlo = fmaxf(dz0, dzn - ceilf(C / slope) - 1.f);
+        }
+        if (!(wlo <= whi)) { wlo = dz0; whi = dzn; }   // non-finite slope etc.: whole range
     }
     const float b2 = beta * 1.4426950408889634f, mb = mn * b2;
+    const int kb0 = (int)(wlo - dz0) >> 4, kb1 = (int)(whi - dz0) >> 4;
+    const int base = kb0 * 16;
+    const int nrb = kb1 - kb0 + 1;
+    const float dzb0 = dz0 + (float)base;
     float bs[16];
     float tot = 0.f;
 #pragma unroll
     for (int b = 0; b < 16; ++b) {
         float acc = 0.f;
-        if (b * 16 < n) {
+        if (b < nrb) {
+            const float a0 = dzb0 + (float)(b * 16);
+            if (base + b * 16 + 15 < n) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int idx = b * 16 + j;
-                const float dz = dz0 + (float)idx;
-                const float w = ex2_ftz(fmaf(-dz * fmaf(d, dz, c1), b2, mb));
-                acc += (idx < n) ? w : 0.f;
+                for (int j = 0; j < 16; ++j) acc += quio_w(a0 + (float)j, d, c1, b2, mb);
+            } else {
+                const int cnt = n - (base + b * 16);
+                for (int j = 0; j < cnt; ++j) acc += quio_w(a0 + (float)j, d, c1, b2, mb);
             }
         }
         bs[b] = acc;
@@ -435,18 +560,30 @@ __device__ __forceinline__ long long heat_bath_quio_f32_small(float f, float d, 
     int sel = -1;
 #pragma unroll
     for (int b = 0; b < 16; ++b) {
-        if (sel < 0) {
+        if (sel < 0 && b < nrb) {
             const float nxt = run + bs[b];
-            if (nxt >= thr && b * 16 < n) sel = b;
+            if (nxt >= thr) sel = b;
             else run = nxt;
         }
     }
-    if (sel < 0) return lo + (long long)width;
-    const int last = min(sel * 16 + 15, n - 1);
-    for (int idx = sel * 16; idx <= last; ++idx) {
-        const float dz = dz0 + (float)idx;
-        run += ex2_ftz(fmaf(-dz * fmaf(d, dz, c1), b2, mb));
-        if (run >= thr) return lo + (long long)idx;
+    if (sel < 0) {  // rounding left the threshold above the window: take its last block
+        float before = 0.f, acc = 0.f;
+#pragma unroll
+        for (int b = 0; b < 16; ++b) {
+            if (b < nrb) {
+                sel = b;
+                before = acc;
+                acc += bs[b];
+            }
+        }
+        run = before;
+    }
+    const int first = base + sel * 16;
+    const int last = min(first + 15, n - 1);
+    const float a0 = dz0 + (float)first;
+    for (int j = 0; j <= last - first; ++j) {
+        run += quio_w(a0 + (float)j, d, c1, b2, mb);
+        if (run >= thr) return lo + (long long)(first + j);
     }
     return lo + (long long)last;
 }
@@ -604,14 +741,67 @@ __device__ void huio_recompute(const DevModel& m, const Z* zs, F* cache, int t, 
 
 // ------------------------------------------------------------------ cache update
 // QUIO (Sect. 3.2): z_s += dz changes f_j by J_sj dz for every neighbour j.
+// Strided form, used by the cooperative path.
 template <class F>
 __device__ __forceinline__ void quio_update_range(const DevModel& m, F* cache, int begin, int end, int stride,
                                                   long long dz) {
     if constexpr (Num<F>::is_float) {
-        const float d = (float)dz;
+        const float d = (float)(int)dz;
         for (int e = begin; e < end; e += stride) atomic_add_field(cache + m.adj_col[e], __ldg(m.adj_f + e) * d);
     } else {
         for (int e = begin; e < end; e += stride) atomic_add_field(cache + m.adj_col[e], m.adj_i[e] * dz);
+    }
+}
+
+// One thread, whole row: rows are padded to multiples of 4 entries and start on
+// 16-byte boundaries, so 16 entries arrive in one round of vector loads that is
+// issued before any of their atomics.
+template <class F>
+__device__ __forceinline__ void quio_update_row(const DevModel& m, F* cache, int begin, int len, long long dz) {
+    const int4* cp = reinterpret_cast<const int4*>(m.adj_col + begin);
+    const int nq = (len + 3) >> 2;
+    if constexpr (Num<F>::is_float) {
+        const float d = (float)(int)dz;
+        const float4* vp = reinterpret_cast<const float4*>(m.adj_f + begin);
+        for (int q0 = 0; q0 < nq; q0 += 4) {
+            int4 c[4];
+            float4 w[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (q0 + u < nq) {
+                    c[u] = __ldg(cp + q0 + u);
+                    w[u] = __ldg(vp + q0 + u);
+                }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = 4 * (q0 + u);
+                if (e + 0 < len) atomic_add_field(cache + c[u].x, w[u].x * d);
+                if (e + 1 < len) atomic_add_field(cache + c[u].y, w[u].y * d);
+                if (e + 2 < len) atomic_add_field(cache + c[u].z, w[u].z * d);
+                if (e + 3 < len) atomic_add_field(cache + c[u].w, w[u].w * d);
+            }
+        }
+    } else {
+        const longlong2* vp = reinterpret_cast<const longlong2*>(m.adj_i + begin);
+        for (int q0 = 0; q0 < nq; q0 += 2) {
+            int4 c[2];
+            longlong2 w[4];
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+                if (q0 + u < nq) {
+                    c[u] = __ldg(cp + q0 + u);
+                    w[2 * u] = __ldg(vp + 2 * (q0 + u));
+                    w[2 * u + 1] = __ldg(vp + 2 * (q0 + u) + 1);
+                }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int e = 4 * (q0 + u);
+                if (e + 0 < len) atomic_add_field(cache + c[u].x, w[2 * u].x * dz);
+                if (e + 1 < len) atomic_add_field(cache + c[u].y, w[2 * u].y * dz);
+                if (e + 2 < len) atomic_add_field(cache + c[u].z, w[2 * u + 1].x * dz);
+                if (e + 3 < len) atomic_add_field(cache + c[u].w, w[2 * u + 1].y * dz);
+            }
+        }
     }
 }
 
@@ -739,88 +929,135 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepArgs a) {
     }
 
     unsigned long long changes = 0;
-    long long gl = 0;  // global level counter (parity of list counters)
+    int gl3 = 0;  // level counter mod 3: which cooperative-list counter is live
+
+    // Decision for one record (reads replica state only).
+    auto decide = [&](const LevelRec& rc, int s, float beta, float ratio, long long& z, long long& v, F& de) {
+        const int k = rc.k;
+        const long long lo = rc.lo;
+        const long long zo = (long long)zs[k];
+        z = lo + zo;
+        v = z;
+        de = F(0);
+        if (rc.width == 0) return;
+        const Words4 x = philox4x32_10((uint32_t)k, (uint32_t)s, (uint32_t)r, a.inst, a.key0, a.key1);
+        VarView<F, KIND> vv;
+        if constexpr (KIND == KIND_QUIO) {
+            vv.f = cache[k];
+            if constexpr (Num<F>::is_float) vv.d = __uint_as_float(rc.aux0);
+            else vv.d = (long long)(((unsigned long long)rc.aux1 << 32) | rc.aux0);
+        } else {
+            vv.a = cache + rc.slot_base;
+            vv.omega = ((uint64_t)rc.aux1 << 32) | rc.aux0;
+        }
+        const long long hi = lo + (long long)rc.width;
+        if constexpr (RULE == RULE_HEAT_BATH) {
+            if (vv.linear()) {
+                v = heat_bath_linear(Num<F>::to_f(vv.lin_coef()), lo, rc.width, x.x0, beta);
+            } else {
+                bool done = false;
+                if constexpr (Num<F>::is_float && KIND == KIND_QUIO) {
+                    if (rc.width < 256u && lo > -(1 << 22) && hi < (1 << 22)) {
+                        v = heat_bath_quio_f32_small((float)vv.f, (float)vv.d, z, lo, rc.width, x.x0, beta);
+                        done = true;
+                    }
+                }
+                if (!done) v = heat_bath_general<F, KIND>(vv, z, lo, rc.width, x.x0, beta);
+            }
+            if (v != z) de = vv.delta(z, v);
+        } else {
+            long long prop;
+            if (RULE == RULE_OPT && unit_open_right(x.x2) < ratio) {
+                prop = opt_argmin<F, KIND>(vv, z, lo, hi);
+            } else {
+                const uint32_t j = pick_below(x.x0, rc.width);
+                prop = lo + (long long)(j >= (uint32_t)zo ? j + 1u : j);
+            }
+            const F dprop = vv.delta(z, prop);
+            if (metropolis_accept<F>(dprop, x.x1, beta)) {
+                v = prop;
+                de = dprop;
+            }
+        }
+    };
+    // Applies a decision: state, energy, counters and the neighbours' caches
+    // (inline for short incidence lists, else through the cooperative list).
+    auto apply = [&](const LevelRec& rc, int s, long long z, long long v, F de, int* cnt_now) {
+        const int k = rc.k;
+        if (v != z) {
+            zs[k] = (Z)(v - (long long)rc.lo);
+            eacc += (Acc)de;
+            ++changes;
+            const int len = rc.link_len;
+            bool inline_upd = len <= a.heavy_links;
+            if (!inline_upd) {
+                const int idx = atomicAdd(cnt_now, 1);
+                if (idx < a.list_cap) {
+                    list[3 * idx + 0] = k;
+                    list[3 * idx + 1] = (int)z;
+                    list[3 * idx + 2] = (int)v;
+                } else {
+                    inline_upd = true;
+                }
+            }
+            if (inline_upd) {
+                if constexpr (KIND == KIND_QUIO)
+                    quio_update_row<F>(m, cache, rc.link_begin, len, v - z);
+                else
+                    huio_update_range<F, Z>(m, zs, cache, k, rc.link_begin, rc.link_begin + len, 1, z, v);
+            }
+        }
+        if (a.trace != nullptr && r < a.trace_R) a.trace[((size_t)s * a.trace_R + r) * m.n + k] = (int32_t)v;
+    };
+    auto load_rec = [&](int i) -> LevelRec {
+        const int4* p = reinterpret_cast<const int4*>(m.lvl_rec + i);
+        const int4 x0 = __ldg(p), x1 = __ldg(p + 1);
+        LevelRec q;
+        q.k = x0.x; q.lo = x0.y; q.width = (uint32_t)x0.z; q.link_begin = x0.w;
+        q.link_len = x1.x; q.slot_base = x1.y; q.aux0 = (uint32_t)x1.z; q.aux1 = (uint32_t)x1.w;
+        return q;
+    };
+
+    // records of the current level's first two items per thread, prefetched
+    // one level ahead
+    int lb = __ldg(m.lvl_ptr), le = __ldg(m.lvl_ptr + 1);
+    LevelRec ra{}, rb{};
+    if (lb + t < le) ra = load_rec(lb + t);
+    if (lb + t + tpr < le) rb = load_rec(lb + t + tpr);
 
     for (int s = 0; s < a.S; ++s) {
         const float beta = __ldg(a.beta + s);
         const float ratio = __ldg(a.ratio + s);
-        for (int L = 0; L < m.n_levels; ++L, ++gl) {
-            int* cnt_now = ctl + (int)(gl % 3);
-            if (t == 0) ctl[(int)((gl + 1) % 3)] = 0;
-            const int lb = __ldg(m.lvl_ptr + L), le = __ldg(m.lvl_ptr + L + 1);
-            for (int i = lb + t; i < le; i += tpr) {
-                const int k = __ldg(m.lvl_vars + i);
-                const VarMeta mt = m.meta[k];
-                const long long lo = mt.lo;
-                const long long zo = (long long)zs[k];
-                const long long z = lo + zo;
-                long long v = z;
-                F de = F(0);
-                if (mt.width != 0) {
-                    const Words4 x = philox4x32_10((uint32_t)k, (uint32_t)s, (uint32_t)r, a.inst, a.key0, a.key1);
-                    VarView<F, KIND> vv;
-                    if constexpr (KIND == KIND_QUIO) {
-                        vv.f = cache[k];
-                        vv.d = Coef<F>::diag(m, k);
-                    } else {
-                        vv.a = cache + m.slot_base[k];
-                        vv.omega = m.omega[k];
-                    }
-                    const long long hi = lo + (long long)mt.width;
-                    if constexpr (RULE == RULE_HEAT_BATH) {
-                        if (vv.linear()) {
-                            v = heat_bath_linear(Num<F>::to_f(vv.lin_coef()), lo, mt.width, x.x0, beta);
-                        } else {
-                            bool done = false;
-                            if constexpr (Num<F>::is_float && KIND == KIND_QUIO) {
-                                if (mt.width < 256u && lo > -(1 << 22) && hi < (1 << 22)) {
-                                    v = heat_bath_quio_f32_small((float)vv.f, (float)vv.d, z, lo, mt.width, x.x0, beta);
-                                    done = true;
-                                }
-                            }
-                            if (!done) v = heat_bath_general<F, KIND>(vv, z, lo, mt.width, x.x0, beta);
-                        }
-                        if (v != z) de = vv.delta(z, v);
-                    } else {
-                        long long prop;
-                        if (RULE == RULE_OPT && unit_open_right(x.x2) < ratio) {
-                            prop = opt_argmin<F, KIND>(vv, z, lo, hi);
-                        } else {
-                            const uint32_t j = pick_below(x.x0, mt.width);
-                            prop = lo + (long long)(j >= (uint32_t)zo ? j + 1u : j);
-                        }
-                        const F dprop = vv.delta(z, prop);
-                        if (metropolis_accept<F>(dprop, x.x1, beta)) {
-                            v = prop;
-                            de = dprop;
-                        }
-                    }
-                }
-                if (v != z) {
-                    zs[k] = (Z)(v - lo);
-                    eacc += (Acc)de;
-                    ++changes;
-                    const int len = mt.link_len;
-                    bool inline_upd = len <= a.heavy_links;
-                    if (!inline_upd) {
-                        const int idx = atomicAdd(cnt_now, 1);
-                        if (idx < a.list_cap) {
-                            list[3 * idx + 0] = k;
-                            list[3 * idx + 1] = (int)z;
-                            list[3 * idx + 2] = (int)v;
-                        } else {
-                            inline_upd = true;
-                        }
-                    }
-                    if (inline_upd) {
-                        if constexpr (KIND == KIND_QUIO)
-                            quio_update_range<F>(m, cache, mt.link_begin, mt.link_begin + len, 1, v - z);
-                        else
-                            huio_update_range<F, Z>(m, zs, cache, k, mt.link_begin, mt.link_begin + len, 1, z, v);
-                    }
-                }
-                if (a.trace != nullptr && r < a.trace_R)
-                    a.trace[((size_t)s * a.trace_R + r) * m.n + k] = (int32_t)v;
+        for (int L = 0; L < m.n_levels; ++L) {
+            int* cnt_now = ctl + gl3;
+            if (t == 0) ctl[gl3 == 2 ? 0 : gl3 + 1] = 0;
+            // prefetch the next level (the first level of the next sweep after the last)
+            int Ln = L + 1;
+            bool more = true;
+            if (Ln == m.n_levels) {
+                Ln = 0;
+                more = (s + 1 < a.S);
+            }
+            int lbn = 0, len = 0;
+            LevelRec na{}, nb{};
+            bool vna = false, vnb = false;
+            if (more) {
+                lbn = __ldg(m.lvl_ptr + Ln);
+                len = __ldg(m.lvl_ptr + Ln + 1);
+                vna = lbn + t < len;
+                vnb = lbn + t + tpr < len;
+                if (vna) na = load_rec(lbn + t);
+                if (vnb) nb = load_rec(lbn + t + tpr);
+            }
+            // one call site: the first two items use the prefetched records
+            for (int j = 0;; ++j) {
+                const int i = lb + t + j * tpr;
+                if (i >= le) break;
+                const LevelRec rc = (j == 0) ? ra : ((j == 1) ? rb : load_rec(i));
+                long long zz, vv2;
+                F d2;
+                decide(rc, s, beta, ratio, zz, vv2, d2);
+                apply(rc, s, zz, vv2, d2, cnt_now);
             }
             named_bar(bar_id, tpr);
             const int cnt = *cnt_now;
@@ -838,6 +1075,9 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepArgs a) {
                 }
                 named_bar(bar_id, tpr);
             }
+            gl3 = gl3 == 2 ? 0 : gl3 + 1;
+            ra = na; rb = nb; lb = lbn; le = len;
+            (void)vna; (void)vnb;
         }
         // ---- FP64 refresh of float fields and energy
         if constexpr (Num<F>::is_float) {
