@@ -93,6 +93,18 @@ sa_status sa_model_create(sa_model** out, int32_t n_vars, const int64_t* lower, 
                           int64_t n_terms, const int64_t* term_offsets, const int32_t* term_vars,
                           const void* coeffs, sa_coef_type coef_type);
 
+/*
+ * sa_model_create_quio_dense -- dense QUIO (Eq. def_QUIO) from a coefficient
+ * matrix: E = sum_k h_k z_k + sum_k J_kk z_k^2 + sum_{i<j} J_ij z_i z_j.
+ *   h  host array of n values, J  host n x n row-major array (both of
+ *   coef_type).  J is read on and above the diagonal only (a symmetric matrix
+ *   counts each unordered pair once, Sect. 2); zero entries are skipped.
+ * Same checks, results and model as sa_model_create with the equivalent term
+ * list, without hashing n^2 terms.
+ */
+sa_status sa_model_create_quio_dense(sa_model** out, int32_t n_vars, const int64_t* lower, const int64_t* upper,
+                                     const void* h, const void* J, sa_coef_type coef_type);
+
 /* Releases the model and its device memory.  NULL is ignored.  The caller must
  * make sure no enqueued work still uses the model. */
 void sa_model_destroy(sa_model* model);
@@ -202,6 +214,55 @@ sa_status sa_run(const sa_model* model, const sa_run_params* params, int32_t* ou
  */
 sa_status sa_energy(const sa_model* model, const int32_t* states, int64_t n_states, void* energies,
                     void* stream);
+
+/*
+ * Batched runs: many instances (models with their own sa_run_params) in one
+ * persistent launch.  This is the replica/instance parallelism of Sect. 4
+ * (independent samples) extended to independent problems; each instance's
+ * results equal those of sa_run with the same parameters (same Philox counters:
+ * set params[i].instance_id to keep streams distinct across instances).
+ *
+ * sa_batch_create  models: n_models model pointers; params: one sa_run_params
+ *                  per model.  All models share one kind (QUIO or HUIO) and one
+ *                  coefficient class (integer or float), and all params one rule
+ *                  (SA_ERR_UNSUPPORTED otherwise).  n_sweeps, n_replicas, seed,
+ *                  instance_id, temperatures and init_states (device memory) may
+ *                  differ per instance; trace must be NULL.  The batch owns its
+ *                  device buffers (arguments, schedules, outputs) and a CUDA
+ *                  graph holding the launch.  Synchronous.
+ * sa_batch_autotune  times the launch with threads_per_replica in
+ *                  {32, 64, 96, 128, 256} (replicas per block: as many as shared
+ *                  memory holds) on a run truncated to trial_sweeps sweeps on
+ *                  `stream`, keeps the fastest shape and re-captures the graph.
+ *                  It overwrites the batch outputs.  Synchronous.
+ * sa_batch_run     replays the graph on `stream` (asynchronous).
+ * sa_batch_result  copies instance i's final states (int32[R_i][N_i]),
+ *                  energies (int64 or double [R_i]) and change counts
+ *                  (uint64[R_i]) into host or device buffers (any may be NULL);
+ *                  synchronises `stream`.
+ * sa_batch_destroy releases everything (NULL is ignored).
+ */
+typedef struct sa_batch sa_batch;
+typedef struct {
+    int32_t n_instances;
+    int32_t n_units;              /* replicas over all instances */
+    int32_t replicas_per_block;
+    int32_t threads_per_replica;
+    int32_t blocks;               /* persistent grid */
+    int32_t state_in_global;
+    int64_t attempts;             /* sum over instances of N R S */
+    int64_t device_bytes;
+    float autotune_ms;            /* best trial time of the last sa_batch_autotune */
+    int32_t _reserved;
+} sa_batch_info;
+sa_status sa_batch_create(sa_batch** out, const sa_model* const* models, int32_t n_models,
+                          const sa_run_params* params);
+sa_status sa_batch_autotune(sa_batch* batch, int32_t trial_sweeps, void* stream);
+sa_status sa_batch_run(sa_batch* batch, void* stream);
+sa_status sa_batch_result(const sa_batch* batch, int32_t instance, int32_t* states, void* energies,
+                          uint64_t* accepts, void* stream);
+sa_status sa_batch_get_info(const sa_batch* batch, sa_batch_info* info);
+void sa_batch_destroy(sa_batch* batch);
 
 /*
  * sa_run_noalloc -- the run of sa_run for callers that must not allocate

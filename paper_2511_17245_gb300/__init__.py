@@ -8,13 +8,15 @@ C entry points; it performs no arithmetic of the method.
 from __future__ import annotations
 
 from . import _lib
-from ._lib import (RULES, SAError, make_params, sa_default_temperatures, sa_energy, sa_last_error,
-                   sa_model_create, sa_model_destroy, sa_model_get_info, sa_run, sa_run_noalloc, sa_run_report,
-                   sa_version)
+from ._lib import (RULES, SAError, make_params, sa_batch_autotune, sa_batch_create, sa_batch_destroy,
+                   sa_batch_get_info, sa_batch_result, sa_batch_run, sa_default_temperatures, sa_energy,
+                   sa_last_error, sa_model_create, sa_model_create_quio_dense, sa_model_destroy, sa_model_get_info,
+                   sa_run, sa_run_noalloc, sa_run_report, sa_version)
 
-__all__ = ["Model", "RULES", "SAError", "make_params", "sa_default_temperatures", "sa_energy", "sa_last_error",
-           "sa_model_create", "sa_model_destroy", "sa_model_get_info", "sa_run", "sa_run_noalloc", "sa_run_report",
-           "sa_version"]
+__all__ = ["Model", "RULES", "SAError", "make_params", "sa_batch_autotune", "sa_batch_create", "sa_batch_destroy",
+           "sa_batch_get_info", "sa_batch_result", "sa_batch_run", "sa_default_temperatures", "sa_energy",
+           "sa_last_error", "sa_model_create", "sa_model_create_quio_dense", "sa_model_destroy",
+           "sa_model_get_info", "sa_run", "sa_run_noalloc", "sa_run_report", "sa_version"]
 
 
 class Model:
@@ -22,8 +24,12 @@ class Model:
 
     def __init__(self, inst):
         self.n = int(inst["n_vars"])
-        self.handle = sa_model_create(inst["n_vars"], inst["lower"], inst["upper"], inst["term_offsets"],
-                                      inst["term_vars"], inst["coeffs"], inst["coef_type"])
+        if "J" in inst:   # dense QUIO spec
+            self.handle = sa_model_create_quio_dense(inst["n_vars"], inst["lower"], inst["upper"], inst["h"],
+                                                     inst["J"], inst["coef_type"])
+        else:
+            self.handle = sa_model_create(inst["n_vars"], inst["lower"], inst["upper"], inst["term_offsets"],
+                                          inst["term_vars"], inst["coeffs"], inst["coef_type"])
         self.info = sa_model_get_info(self.handle)
         self.is_float = bool(self.info["is_float"])
 

@@ -45,6 +45,13 @@ class sa_run_report(C.Structure):
                 ("blocks", C.c_int32), ("n_levels", C.c_int32), ("kernel_ms", C.c_float), ("_reserved", C.c_int32)]
 
 
+class sa_batch_info(C.Structure):
+    _fields_ = [("n_instances", C.c_int32), ("n_units", C.c_int32), ("replicas_per_block", C.c_int32),
+                ("threads_per_replica", C.c_int32), ("blocks", C.c_int32), ("state_in_global", C.c_int32),
+                ("attempts", C.c_int64), ("device_bytes", C.c_int64), ("autotune_ms", C.c_float),
+                ("_reserved", C.c_int32)]
+
+
 class sa_run_params(C.Structure):
     _fields_ = [("rule", C.c_int32), ("n_sweeps", C.c_int32), ("n_replicas", C.c_int32),
                 ("refresh_interval", C.c_int32), ("seed", C.c_uint64), ("t_max", C.c_double),
@@ -57,7 +64,9 @@ class sa_run_params(C.Structure):
 
 # Every symbol include/sa.h declares (checked by the tests).
 EXPORTS = ["sa_model_create", "sa_model_destroy", "sa_model_get_info", "sa_default_temperatures",
-           "sa_run", "sa_energy", "sa_last_error", "sa_version", "sa_run_noalloc"]
+           "sa_run", "sa_energy", "sa_last_error", "sa_version", "sa_run_noalloc", "sa_model_create_quio_dense",
+           "sa_batch_create", "sa_batch_autotune", "sa_batch_run", "sa_batch_result", "sa_batch_get_info",
+           "sa_batch_destroy"]
 # size of the fixed device scratch array behind sa_run_noalloc (SA_NOALLOC_SCRATCH_BYTES)
 NOALLOC_SCRATCH_BYTES = 4 << 20
 
@@ -85,6 +94,20 @@ def load():
         lib.sa_run.restype = C.c_int
         lib.sa_run_noalloc.argtypes = [P, C.POINTER(sa_run_params), P, P, P, P]
         lib.sa_run_noalloc.restype = C.c_int
+        lib.sa_model_create_quio_dense.argtypes = [C.POINTER(C.c_void_p), C.c_int32, P, P, P, P, C.c_int]
+        lib.sa_model_create_quio_dense.restype = C.c_int
+        lib.sa_batch_create.argtypes = [C.POINTER(C.c_void_p), P, C.c_int32, P]
+        lib.sa_batch_create.restype = C.c_int
+        lib.sa_batch_autotune.argtypes = [P, C.c_int32, P]
+        lib.sa_batch_autotune.restype = C.c_int
+        lib.sa_batch_run.argtypes = [P, P]
+        lib.sa_batch_run.restype = C.c_int
+        lib.sa_batch_result.argtypes = [P, C.c_int32, P, P, P, P]
+        lib.sa_batch_result.restype = C.c_int
+        lib.sa_batch_get_info.argtypes = [P, C.POINTER(sa_batch_info)]
+        lib.sa_batch_get_info.restype = C.c_int
+        lib.sa_batch_destroy.argtypes = [P]
+        lib.sa_batch_destroy.restype = None
         lib.sa_energy.argtypes = [P, P, C.c_int64, P, P]
         lib.sa_energy.restype = C.c_int
         lib.sa_last_error.argtypes = []
@@ -191,3 +214,51 @@ def sa_run_noalloc(h, params: sa_run_params, out_states, out_energies, out_accep
 
 def sa_energy(h, states, n_states, energies, stream=None):
     _check(load().sa_energy(h, ptr(states), int(n_states), ptr(energies), stream))
+
+
+def sa_model_create_quio_dense(n_vars, lower, upper, h, J, coef_type):
+    """Dense QUIO model from h[n] and the row-major n x n matrix J (upper triangle read)."""
+    lib = load()
+    ct = COEF[coef_type] if isinstance(coef_type, str) else int(coef_type)
+    dt = {0: np.int32, 1: np.int64, 2: np.float32, 3: np.float64}[ct]
+    lower = np.ascontiguousarray(lower, np.int64)
+    upper = np.ascontiguousarray(upper, np.int64)
+    h = np.ascontiguousarray(h, dt)
+    J = np.ascontiguousarray(J, dt)
+    out = C.c_void_p()
+    _check(lib.sa_model_create_quio_dense(C.byref(out), int(n_vars), ptr(lower), ptr(upper), ptr(h), ptr(J), ct))
+    return out.value
+
+
+def sa_batch_create(handles, params_list):
+    """handles: model handles; params_list: sa_run_params, one per model."""
+    lib = load()
+    n = len(handles)
+    harr = (C.c_void_p * n)(*handles)
+    parr = (sa_run_params * n)(*params_list)
+    out = C.c_void_p()
+    _check(lib.sa_batch_create(C.byref(out), C.cast(harr, C.c_void_p), n, C.cast(parr, C.c_void_p)))
+    return out.value
+
+
+def sa_batch_autotune(b, trial_sweeps, stream=None):
+    _check(load().sa_batch_autotune(b, int(trial_sweeps), stream))
+
+
+def sa_batch_run(b, stream=None):
+    _check(load().sa_batch_run(b, stream))
+
+
+def sa_batch_result(b, i, states=None, energies=None, accepts=None, stream=None):
+    _check(load().sa_batch_result(b, int(i), ptr(states), ptr(energies), ptr(accepts), stream))
+
+
+def sa_batch_get_info(b) -> dict:
+    info = sa_batch_info()
+    _check(load().sa_batch_get_info(b, C.byref(info)))
+    return {f: getattr(info, f) for f, _ in info._fields_}
+
+
+def sa_batch_destroy(b):
+    if b:
+        load().sa_batch_destroy(b)

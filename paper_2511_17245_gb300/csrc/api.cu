@@ -61,8 +61,20 @@ struct Member {
     int32_t exp;
 };
 
+// View of a term's members inside a shared pool.
+struct MSpan {
+    const Member* p = nullptr;
+    size_t n = 0;
+    const Member* begin() const { return p; }
+    const Member* end() const { return p + n; }
+    size_t size() const { return n; }
+    const Member& operator[](size_t i) const { return p[i]; }
+};
+
 struct MergedTerm {
-    std::vector<Member> mem;  // distinct variables, sorted
+    int64_t moff = 0;         // first member in the pool
+    int32_t nmem = 0;
+    MSpan mem;                // distinct variables, sorted (set once the pool is final)
     __int128 ci;
     double cf;
     int order() const {
@@ -95,6 +107,7 @@ struct sa_model {
     int64_t cache_elems = 0;
     int32_t max_link_len = 0;
     double de_max = 0.0, de_min = 0.0;
+    bool f32_coeffs = false;   // coefficients given as fp32: the FP64 refresh promotes the fp32 values
 };
 
 namespace {
@@ -140,79 +153,13 @@ void build_levels(int32_t n, const std::vector<int64_t>& nb_ptr, const std::vect
     for (int32_t k = 0; k < n; ++k) lvl_vars[fill[level[k]]++] = k;
 }
 
-sa_status compile_model(sa_model* M, int32_t n, const int64_t* lower, const int64_t* upper, int64_t n_terms,
-                        const int64_t* term_offsets, const int32_t* term_vars, const void* coeffs,
-                        sa_coef_type ct) {
-    M->n = n;
-    M->is_float = (ct == SA_COEF_F32 || ct == SA_COEF_F64);
-    std::vector<int32_t> lo(n);
-    std::vector<uint32_t> width(n);
-    for (int32_t k = 0; k < n; ++k) {
-        if (lower[k] > upper[k]) return fail(SA_ERR_INVALID, "lower bound above upper bound at variable " + std::to_string(k));
-        if (lower[k] < INT32_MIN || upper[k] > INT32_MAX)
-            return fail(SA_ERR_UNSUPPORTED, "bounds must fit int32 (variable " + std::to_string(k) + ")");
-        if (upper[k] - lower[k] > (int64_t)INT32_MAX)
-            return fail(SA_ERR_INVALID, "range u-l must be below 2^31 (variable " + std::to_string(k) + ")");
-        lo[k] = (int32_t)lower[k];
-        width[k] = (uint32_t)(upper[k] - lower[k]);
-        M->max_width = std::max(M->max_width, width[k]);
-    }
-    if (term_offsets == nullptr && n_terms > 0) return fail(SA_ERR_INVALID, "term_offsets is NULL");
-    if (n_terms > 0 && term_offsets[0] != 0) return fail(SA_ERR_INVALID, "term_offsets[0] must be 0");
-    for (int64_t t = 0; t < n_terms; ++t)
-        if (term_offsets[t + 1] < term_offsets[t]) return fail(SA_ERR_INVALID, "term_offsets must be non-decreasing");
-    const int64_t flat = n_terms > 0 ? term_offsets[n_terms] : 0;
-    for (int64_t j = 0; j < flat; ++j)
-        if (term_vars[j] < 0 || term_vars[j] >= n) return fail(SA_ERR_INVALID, "variable index out of range in term list");
-
-    // ---- merge equal multisets (Sect. 2)
-    std::unordered_map<std::string, size_t> index;
-    std::vector<MergedTerm> terms;
-    __int128 const_i = 0;
-    double const_d = 0.0;
-    std::vector<int32_t> buf;
-    for (int64_t t = 0; t < n_terms; ++t) {
-        __int128 ci = 0;
-        double cf = 0.0;
-        switch (ct) {
-        case SA_COEF_I32: ci = ((const int32_t*)coeffs)[t]; break;
-        case SA_COEF_I64: ci = ((const int64_t*)coeffs)[t]; break;
-        case SA_COEF_F32: cf = ((const float*)coeffs)[t]; break;
-        case SA_COEF_F64: cf = ((const double*)coeffs)[t]; break;
-        default: return fail(SA_ERR_INVALID, "unknown coefficient type");
-        }
-        if (M->is_float && !std::isfinite(cf)) return fail(SA_ERR_INVALID, "non-finite coefficient in term " + std::to_string(t));
-        buf.assign(term_vars + term_offsets[t], term_vars + term_offsets[t + 1]);
-        if (buf.empty()) {
-            const_i += ci;
-            const_d += cf;
-            continue;
-        }
-        std::sort(buf.begin(), buf.end());
-        std::string key(reinterpret_cast<const char*>(buf.data()), buf.size() * sizeof(int32_t));
-        auto it = index.find(key);
-        MergedTerm* cur;
-        if (it == index.end()) {
-            MergedTerm mt;
-            for (size_t i = 0; i < buf.size();) {
-                size_t j = i;
-                while (j < buf.size() && buf[j] == buf[i]) ++j;
-                mt.mem.push_back({buf[i], (int32_t)(j - i)});
-                i = j;
-            }
-            mt.ci = ci;
-            mt.cf = cf;
-            index.emplace(std::move(key), terms.size());
-            terms.push_back(std::move(mt));
-            cur = &terms.back();
-        } else {
-            cur = &terms[it->second];
-            cur->ci += ci;
-            cur->cf += cf;
-        }
-        const __int128 lim = (__int128)1 << 100;
-        if (!M->is_float && (cur->ci > lim || cur->ci < -lim)) return fail(SA_ERR_OVERFLOW, "merged coefficient overflows");
-    }
+// Second half of model compilation, shared by the term-list and dense entry
+// points: drops zero terms, classifies, checks the int64 bounds, derives the
+// Sect. 3.4 temperatures and lays the model out on the device.
+sa_status compile_terms(sa_model* M, int32_t n, const int64_t* lower, const int64_t* upper,
+                        const std::vector<int32_t>& lo, const std::vector<uint32_t>& width,
+                        std::vector<MergedTerm>& terms, std::vector<Member>& pool, __int128 const_i, double const_d) {
+    for (auto& t : terms) t.mem = MSpan{pool.data() + t.moff, (size_t)t.nmem};
     // drop zero terms
     std::vector<MergedTerm> kept;
     kept.reserve(terms.size());
@@ -348,6 +295,7 @@ sa_status compile_model(sa_model* M, int32_t n, const int64_t* lower, const int6
         }
         // sort each row by column for locality
         for (int32_t k = 0; k < n; ++k) {
+            if (std::is_sorted(col.begin() + ptr[k], col.begin() + ptr[k] + deg[k])) continue;
             std::vector<int64_t> order(deg[k]);
             for (size_t i = 0; i < order.size(); ++i) order[i] = ptr[k] + (int64_t)i;
             std::sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return col[x] < col[y]; });
@@ -412,7 +360,8 @@ sa_status compile_model(sa_model* M, int32_t n, const int64_t* lower, const int6
             std::vector<float> vf(vd.size()), lf(n), df(n);
             for (size_t i = 0; i < vd.size(); ++i) vf[i] = (float)vd[i];
             for (int32_t k = 0; k < n; ++k) { lf[k] = (float)lin_d[k]; df[k] = (float)diag_d[k]; }
-            off.adj_f = blob.add(vf); off.adj_d = blob.add(vd);
+            off.adj_f = blob.add(vf);
+            off.adj_d = M->f32_coeffs ? SIZE_MAX : blob.add(vd);
             off.lin_f = blob.add(lf); off.lin_d = blob.add(lin_d);
             off.diag_f = blob.add(df); off.diag_d = blob.add(diag_d);
         } else {
@@ -543,7 +492,8 @@ sa_status compile_model(sa_model* M, int32_t n, const int64_t* lower, const int6
     if (dm.kind == sa::KIND_QUIO) {
         dm.adj_col = at<int32_t>(b, off.adj_col);
         if (M->is_float) {
-            dm.adj_f = at<float>(b, off.adj_f); dm.adj_d = at<double>(b, off.adj_d);
+            dm.adj_f = at<float>(b, off.adj_f);
+            dm.adj_d = off.adj_d == SIZE_MAX ? nullptr : at<double>(b, off.adj_d);
             dm.lin_f = at<float>(b, off.lin_f); dm.lin_d = at<double>(b, off.lin_d);
             dm.diag_f = at<float>(b, off.diag_f); dm.diag_d = at<double>(b, off.diag_d);
         } else {
@@ -566,6 +516,87 @@ sa_status compile_model(sa_model* M, int32_t n, const int64_t* lower, const int6
         }
     }
     return SA_OK;
+}
+
+
+sa_status compile_model(sa_model* M, int32_t n, const int64_t* lower, const int64_t* upper, int64_t n_terms,
+                        const int64_t* term_offsets, const int32_t* term_vars, const void* coeffs,
+                        sa_coef_type ct) {
+    M->n = n;
+    M->is_float = (ct == SA_COEF_F32 || ct == SA_COEF_F64);
+    M->f32_coeffs = (ct == SA_COEF_F32);
+    std::vector<int32_t> lo(n);
+    std::vector<uint32_t> width(n);
+    for (int32_t k = 0; k < n; ++k) {
+        if (lower[k] > upper[k]) return fail(SA_ERR_INVALID, "lower bound above upper bound at variable " + std::to_string(k));
+        if (lower[k] < INT32_MIN || upper[k] > INT32_MAX)
+            return fail(SA_ERR_UNSUPPORTED, "bounds must fit int32 (variable " + std::to_string(k) + ")");
+        if (upper[k] - lower[k] > (int64_t)INT32_MAX)
+            return fail(SA_ERR_INVALID, "range u-l must be below 2^31 (variable " + std::to_string(k) + ")");
+        lo[k] = (int32_t)lower[k];
+        width[k] = (uint32_t)(upper[k] - lower[k]);
+        M->max_width = std::max(M->max_width, width[k]);
+    }
+    if (term_offsets == nullptr && n_terms > 0) return fail(SA_ERR_INVALID, "term_offsets is NULL");
+    if (n_terms > 0 && term_offsets[0] != 0) return fail(SA_ERR_INVALID, "term_offsets[0] must be 0");
+    for (int64_t t = 0; t < n_terms; ++t)
+        if (term_offsets[t + 1] < term_offsets[t]) return fail(SA_ERR_INVALID, "term_offsets must be non-decreasing");
+    const int64_t flat = n_terms > 0 ? term_offsets[n_terms] : 0;
+    for (int64_t j = 0; j < flat; ++j)
+        if (term_vars[j] < 0 || term_vars[j] >= n) return fail(SA_ERR_INVALID, "variable index out of range in term list");
+
+    // ---- merge equal multisets (Sect. 2)
+    std::unordered_map<std::string, size_t> index;
+    std::vector<MergedTerm> terms;
+    std::vector<Member> pool;
+    __int128 const_i = 0;
+    double const_d = 0.0;
+    std::vector<int32_t> buf;
+    for (int64_t t = 0; t < n_terms; ++t) {
+        __int128 ci = 0;
+        double cf = 0.0;
+        switch (ct) {
+        case SA_COEF_I32: ci = ((const int32_t*)coeffs)[t]; break;
+        case SA_COEF_I64: ci = ((const int64_t*)coeffs)[t]; break;
+        case SA_COEF_F32: cf = ((const float*)coeffs)[t]; break;
+        case SA_COEF_F64: cf = ((const double*)coeffs)[t]; break;
+        default: return fail(SA_ERR_INVALID, "unknown coefficient type");
+        }
+        if (M->is_float && !std::isfinite(cf)) return fail(SA_ERR_INVALID, "non-finite coefficient in term " + std::to_string(t));
+        buf.assign(term_vars + term_offsets[t], term_vars + term_offsets[t + 1]);
+        if (buf.empty()) {
+            const_i += ci;
+            const_d += cf;
+            continue;
+        }
+        std::sort(buf.begin(), buf.end());
+        std::string key(reinterpret_cast<const char*>(buf.data()), buf.size() * sizeof(int32_t));
+        auto it = index.find(key);
+        MergedTerm* cur;
+        if (it == index.end()) {
+            MergedTerm mt;
+            mt.moff = (int64_t)pool.size();
+            for (size_t i = 0; i < buf.size();) {
+                size_t j = i;
+                while (j < buf.size() && buf[j] == buf[i]) ++j;
+                pool.push_back({buf[i], (int32_t)(j - i)});
+                i = j;
+            }
+            mt.nmem = (int32_t)(pool.size() - mt.moff);
+            mt.ci = ci;
+            mt.cf = cf;
+            index.emplace(std::move(key), terms.size());
+            terms.push_back(std::move(mt));
+            cur = &terms.back();
+        } else {
+            cur = &terms[it->second];
+            cur->ci += ci;
+            cur->cf += cf;
+        }
+        const __int128 lim = (__int128)1 << 100;
+        if (!M->is_float && (cur->ci > lim || cur->ci < -lim)) return fail(SA_ERR_OVERFLOW, "merged coefficient overflows");
+    }
+    return compile_terms(M, n, lower, upper, lo, width, terms, pool, const_i, const_d);
 }
 
 // RAII holder of stream-ordered device temporaries
@@ -614,6 +645,88 @@ void sa_model_destroy(sa_model* model) {
     if (!model) return;
     if (model->dmem) cudaFree(model->dmem);
     delete model;
+}
+
+sa_status sa_model_create_quio_dense(sa_model** out, int32_t n, const int64_t* lower, const int64_t* upper,
+                                     const void* h, const void* J, sa_coef_type coef_type) {
+    if (out == nullptr) return fail(SA_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (n <= 0) return fail(SA_ERR_INVALID, "n_vars must be positive");
+    if (!lower || !upper || !h || !J) return fail(SA_ERR_INVALID, "NULL argument");
+    if ((int)coef_type < 0 || (int)coef_type > 3) return fail(SA_ERR_INVALID, "unknown coefficient type");
+    sa_model* M = new sa_model();
+    cudaGetDevice(&M->device);
+    M->n = n;
+    M->is_float = (coef_type == SA_COEF_F32 || coef_type == SA_COEF_F64);
+    M->f32_coeffs = (coef_type == SA_COEF_F32);
+    std::vector<int32_t> lo(n);
+    std::vector<uint32_t> width(n);
+    auto bad = [&](sa_status st, const std::string& msg) {
+        delete M;
+        return fail(st, msg);
+    };
+    for (int32_t k = 0; k < n; ++k) {
+        if (lower[k] > upper[k]) return bad(SA_ERR_INVALID, "lower bound above upper bound at variable " + std::to_string(k));
+        if (lower[k] < INT32_MIN || upper[k] > INT32_MAX) return bad(SA_ERR_UNSUPPORTED, "bounds must fit int32");
+        if (upper[k] - lower[k] > (int64_t)INT32_MAX) return bad(SA_ERR_INVALID, "range u-l must be below 2^31");
+        lo[k] = (int32_t)lower[k];
+        width[k] = (uint32_t)(upper[k] - lower[k]);
+        M->max_width = std::max(M->max_width, width[k]);
+    }
+    auto val = [&](const void* a, size_t i, __int128& ci, double& cf) {
+        ci = 0;
+        cf = 0.0;
+        switch (coef_type) {
+        case SA_COEF_I32: ci = ((const int32_t*)a)[i]; break;
+        case SA_COEF_I64: ci = ((const int64_t*)a)[i]; break;
+        case SA_COEF_F32: cf = ((const float*)a)[i]; break;
+        default: cf = ((const double*)a)[i]; break;
+        }
+        return M->is_float ? (cf != 0.0) : (ci != 0);
+    };
+    std::vector<MergedTerm> terms;
+    std::vector<Member> pool;
+    __int128 ci;
+    double cf;
+    for (int32_t k = 0; k < n; ++k) {
+        if (val(h, k, ci, cf)) {
+            if (M->is_float && !std::isfinite(cf)) return bad(SA_ERR_INVALID, "non-finite coefficient");
+            MergedTerm t;
+            t.moff = (int64_t)pool.size();
+            t.nmem = 1;
+            t.ci = ci;
+            t.cf = cf;
+            pool.push_back({k, 1});
+            terms.push_back(t);
+        }
+    }
+    for (int32_t i = 0; i < n; ++i) {
+        for (int32_t j = i; j < n; ++j) {
+            if (!val(J, (size_t)i * n + j, ci, cf)) continue;
+            if (M->is_float && !std::isfinite(cf)) return bad(SA_ERR_INVALID, "non-finite coefficient");
+            MergedTerm t;
+            t.moff = (int64_t)pool.size();
+            t.ci = ci;
+            t.cf = cf;
+            if (i == j) {
+                pool.push_back({i, 2});
+                t.nmem = 1;
+            } else {
+                pool.push_back({i, 1});
+                pool.push_back({j, 1});
+                t.nmem = 2;
+            }
+            terms.push_back(t);
+        }
+    }
+    sa_status st = compile_terms(M, n, lower, upper, lo, width, terms, pool, 0, 0.0);
+    if (st != SA_OK) {
+        if (M->dmem) cudaFree(M->dmem);
+        delete M;
+        return st;
+    }
+    *out = M;
+    return SA_OK;
 }
 
 sa_status sa_model_get_info(const sa_model* M, sa_model_info* info) {

@@ -22,6 +22,21 @@ int launch_sweep(const SweepArgs& a, int zbytes, int rule, bool smem, int blocks
     return launch_sweep_huio_i64(a, zbytes, rule, smem, blocks, threads, shared_bytes, stream);
 }
 
+int launch_batch_quio_i64(const BatchArgs&, int, int, bool, int, int, size_t, void*, bool);
+int launch_batch_quio_f32(const BatchArgs&, int, int, bool, int, int, size_t, void*, bool);
+int launch_batch_huio_i64(const BatchArgs&, int, int, bool, int, int, size_t, void*, bool);
+int launch_batch_huio_f32(const BatchArgs&, int, int, bool, int, int, size_t, void*, bool);
+
+int launch_batch(const BatchArgs& b, int is_float, int kind, int zbytes, int rule, bool smem, int blocks, int threads,
+                 size_t shared_bytes, void* stream, bool set_attr) {
+    if (kind == KIND_QUIO) {
+        if (is_float) return launch_batch_quio_f32(b, zbytes, rule, smem, blocks, threads, shared_bytes, stream, set_attr);
+        return launch_batch_quio_i64(b, zbytes, rule, smem, blocks, threads, shared_bytes, stream, set_attr);
+    }
+    if (is_float) return launch_batch_huio_f32(b, zbytes, rule, smem, blocks, threads, shared_bytes, stream, set_attr);
+    return launch_batch_huio_i64(b, zbytes, rule, smem, blocks, threads, shared_bytes, stream, set_attr);
+}
+
 int sweep_max_shared_optin() {
     int dev = 0, v = 0;
     cudaGetDevice(&dev);
@@ -80,7 +95,8 @@ __global__ void __launch_bounds__(256) energy_kernel(const EnergyArgs a) {
             if (zk < mt.lo || zk > (long long)mt.lo + (long long)mt.width) continue;
             if (IS_FLOAT) {
                 double f = 0.0;
-                for (int e = mt.link_begin; e < mt.link_begin + mt.link_len; ++e) f += m.adj_d[e] * (double)z[m.adj_col[e]];
+                for (int e = mt.link_begin; e < mt.link_begin + mt.link_len; ++e)
+                    f += (m.adj_d ? m.adj_d[e] : (double)m.adj_f[e]) * (double)z[m.adj_col[e]];
                 e_d += (double)zk * (m.lin_d[k] + m.diag_d[k] * (double)zk);
                 p_d += (double)zk * f;
             } else {

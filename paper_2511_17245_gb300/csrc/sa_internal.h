@@ -48,7 +48,7 @@ struct DevModel {
     const int32_t* adj_col;     // symmetric adjacency, both directions
     const int64_t* adj_i;
     const float* adj_f;
-    const double* adj_d;
+    const double* adj_d;        // null when the coefficients were given as fp32
     const int64_t* lin_i;
     const float* lin_f;
     const double* lin_d;
@@ -106,6 +106,23 @@ struct SweepArgs {
     int32_t list_cap;           // capacity of the cooperative update list
 };
 
+// One unit of batched work: one replica of one instance.
+struct BatchUnit {
+    int32_t inst;
+    int32_t replica;
+};
+
+// Arguments of the persistent batched kernel.
+struct BatchArgs {
+    const SweepArgs* insts;     // per-instance arguments (device table)
+    const BatchUnit* units;     // ordered by decreasing cost
+    int32_t n_units;
+    unsigned int* counter;      // next unit (reset to 0 before every launch)
+    int64_t slot_bytes;         // state region of one thread group (max over instances)
+    int32_t rpc, tpr;
+    uint8_t* gstate;            // per-group regions when the state is not on chip
+};
+
 // Arguments of the energy kernel.
 struct EnergyArgs {
     DevModel m;
@@ -133,6 +150,9 @@ struct ModelView {
 int launch_sweep(const SweepArgs& a, int zbytes, int rule, bool smem, int blocks, int threads,
                  size_t shared_bytes, void* stream);
 int launch_energy(const EnergyArgs& a, void* stream);
+// Persistent batched kernel; set_attr = false during stream capture.
+int launch_batch(const BatchArgs& b, int is_float, int kind, int zbytes, int rule, bool smem, int blocks,
+                 int threads, size_t shared_bytes, void* stream, bool set_attr);
 int sweep_max_shared_optin();
 
 }  // namespace sa

@@ -643,7 +643,8 @@ __device__ void quio_recompute(const DevModel& m, const Z* zs, F* cache, int t, 
             double f = m.lin_d[k];
             for (int e = mt.link_begin; e < mt.link_begin + mt.link_len; ++e) {
                 const int j = m.adj_col[e];
-                f += m.adj_d[e] * (double)((long long)m.meta[j].lo + (long long)zs[j]);
+                const double w = m.adj_d ? m.adj_d[e] : (double)m.adj_f[e];
+                f += w * (double)((long long)m.meta[j].lo + (long long)zs[j]);
             }
             const float ff = (float)f;
             if (measure) drift = fmaxf(drift, (float)fabs((double)cache[k] - f));
@@ -874,20 +875,16 @@ __device__ T group_sum(T v, T* red, int t, int tpr, int bar_id) {
     return tot;
 }
 
-// ------------------------------------------------------------------ the kernel
-template <class F, class Z, int RULE, int KIND, bool SMEM>
-__global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepArgs a) {
+// ------------------------------------------------------------------ one replica
+// The whole SA run of replica r (Sect. 3.1) by the `tpr` threads of one group;
+// `base` is the group's state region (shared or global memory).
+template <class F, class Z, int RULE, int KIND>
+__device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot, const int t, const int r,
+                                             uint8_t* base) {
     using Acc = typename Num<F>::Acc;
-    extern __shared__ __align__(16) uint8_t smem_raw[];
     const DevModel& m = a.m;
-    const int slot = threadIdx.x / a.tpr;
-    const int t = threadIdx.x - slot * a.tpr;
-    const int r = blockIdx.x * a.rpc + slot;
-    if (slot >= a.rpc || r >= a.R) return;
     const int bar_id = 1 + slot;
     const int tpr = a.tpr;
-
-    uint8_t* base = SMEM ? (smem_raw + (size_t)slot * (size_t)a.rep_bytes) : (a.gstate + (size_t)r * (size_t)a.rep_bytes);
     Z* zs = reinterpret_cast<Z*>(base + a.off_z);
     F* cache = reinterpret_cast<F*>(base + a.off_cache);
     int* ctl = reinterpret_cast<int*>(base + a.off_ctl);      // [3] list counters
@@ -1118,6 +1115,49 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepArgs a) {
             for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
             if ((t & 31) == 0) atomicMax(a.drift_bits, __float_as_uint(dmax));
         }
+    }
+}
+
+// ------------------------------------------------------------------ kernels
+// One instance: replica blockIdx.x * rpc + slot per thread group.
+template <class F, class Z, int RULE, int KIND, bool SMEM>
+__global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepArgs a) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    const int slot = threadIdx.x / a.tpr;
+    const int t = threadIdx.x - slot * a.tpr;
+    const int r = blockIdx.x * a.rpc + slot;
+    if (slot >= a.rpc || r >= a.R) return;
+    uint8_t* base = SMEM ? (smem_raw + (size_t)slot * (size_t)a.rep_bytes) : (a.gstate + (size_t)r * (size_t)a.rep_bytes);
+    replica_body<F, Z, RULE, KIND>(a, slot, t, r, base);
+}
+
+// Many instances in one persistent launch: every thread group repeatedly claims
+// the next (instance, replica) unit from a global counter (units are ordered by
+// decreasing cost on the host) and runs it with that instance's arguments,
+// copied into shared memory.
+template <class F, class Z, int RULE, int KIND, bool SMEM>
+__global__ void __launch_bounds__(512, 1) batch_kernel(const BatchArgs b) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    __shared__ SweepArgs args_s[15];
+    __shared__ int unit_s[15];
+    const int slot = threadIdx.x / b.tpr;
+    const int t = threadIdx.x - slot * b.tpr;
+    if (slot >= b.rpc) return;
+    const int bar_id = 1 + slot;
+    uint8_t* base = SMEM ? (smem_raw + (size_t)slot * (size_t)b.slot_bytes)
+                         : (b.gstate + ((size_t)blockIdx.x * b.rpc + slot) * (size_t)b.slot_bytes);
+    for (;;) {
+        if (t == 0) unit_s[slot] = (int)atomicAdd(b.counter, 1u);
+        named_bar(bar_id, b.tpr);
+        const int u = unit_s[slot];
+        if (u >= b.n_units) break;
+        const BatchUnit un = b.units[u];
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(b.insts + un.inst);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(&args_s[slot]);
+        for (int w = t; w < (int)(sizeof(SweepArgs) / 4); w += b.tpr) dst[w] = src[w];
+        named_bar(bar_id, b.tpr);
+        replica_body<F, Z, RULE, KIND>(args_s[slot], slot, t, un.replica, base);
+        named_bar(bar_id, b.tpr);   // the group is done with args_s and unit_s
     }
 }
 

@@ -6,4 +6,8 @@ int launch_sweep_huio_i64(const SweepArgs& a, int zbytes, int rule, bool smem, i
                               size_t sh, void* stream) {
     return launch_family<long long, KIND_HUIO>(a, zbytes, rule, smem, blocks, threads, sh, (cudaStream_t)stream);
 }
+int launch_batch_huio_i64(const BatchArgs& b, int zbytes, int rule, bool smem, int blocks, int threads,
+                             size_t sh, void* stream, bool set_attr) {
+    return launch_batch_family<long long, KIND_HUIO>(b, zbytes, rule, smem, blocks, threads, sh, (cudaStream_t)stream, set_attr);
+}
 }  // namespace sa

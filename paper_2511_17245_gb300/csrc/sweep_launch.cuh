@@ -39,4 +39,40 @@ static int launch_family(const SweepArgs& a, int zbytes, int rule, bool smem, in
     return launch_rule<F, uint32_t, KIND, false>(a, rule, blocks, threads, sh, st);
 }
 
+template <class F, class Z, int RULE, int KIND, bool SMEM>
+static int launch_batch_one(const BatchArgs& b, int blocks, int threads, size_t shared_bytes, cudaStream_t st,
+                            bool set_attr) {
+    auto kern = dev::batch_kernel<F, Z, RULE, KIND, SMEM>;
+    if (set_attr) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shared_bytes);
+        if (e != cudaSuccess) return (int)e;
+    }
+    if (blocks == 0) return 0;   // attribute only (before a stream capture)
+    kern<<<blocks, threads, shared_bytes, st>>>(b);
+    return (int)cudaGetLastError();
+}
+
+template <class F, class Z, int KIND, bool SMEM>
+static int launch_batch_rule(const BatchArgs& b, int rule, int blocks, int threads, size_t sh, cudaStream_t st,
+                             bool set_attr) {
+    switch (rule) {
+    case RULE_METROPOLIS: return launch_batch_one<F, Z, RULE_METROPOLIS, KIND, SMEM>(b, blocks, threads, sh, st, set_attr);
+    case RULE_HEAT_BATH: return launch_batch_one<F, Z, RULE_HEAT_BATH, KIND, SMEM>(b, blocks, threads, sh, st, set_attr);
+    default: return launch_batch_one<F, Z, RULE_OPT, KIND, SMEM>(b, blocks, threads, sh, st, set_attr);
+    }
+}
+
+template <class F, int KIND>
+static int launch_batch_family(const BatchArgs& b, int zbytes, int rule, bool smem, int blocks, int threads,
+                               size_t sh, cudaStream_t st, bool set_attr) {
+    if (smem) {
+        if (zbytes == 1) return launch_batch_rule<F, uint8_t, KIND, true>(b, rule, blocks, threads, sh, st, set_attr);
+        if (zbytes == 2) return launch_batch_rule<F, uint16_t, KIND, true>(b, rule, blocks, threads, sh, st, set_attr);
+        return launch_batch_rule<F, uint32_t, KIND, true>(b, rule, blocks, threads, sh, st, set_attr);
+    }
+    if (zbytes == 1) return launch_batch_rule<F, uint8_t, KIND, false>(b, rule, blocks, threads, sh, st, set_attr);
+    if (zbytes == 2) return launch_batch_rule<F, uint16_t, KIND, false>(b, rule, blocks, threads, sh, st, set_attr);
+    return launch_batch_rule<F, uint32_t, KIND, false>(b, rule, blocks, threads, sh, st, set_attr);
+}
+
 }  // namespace sa

@@ -279,26 +279,45 @@ def initial_states(seed: int, inst, n_states: int):
 
 
 # ---------------------------------------------------------------- batches
-def batch_instances(seed: int = 3, n_instances: int = 4096, n_min: int = 50, n_max: int = 2000,
-                    w_min: int = 2, w_max: int = 1024, deg_min: int = 8, deg_max: int = 64):
-    """Uneven instances: N log-uniform, range width log-uniform (lower bound 0),
-    alternating dense (full J) and sparse (degree U{deg_min..deg_max}); fp32
-    J, h ~ N(0,1), J_ii ~ U[0,1].  Returns a list of instance dicts."""
+def batch_specs(seed: int = 3, n_instances: int = 4096, n_min: int = 50, n_max: int = 2000,
+                w_min: int = 2, w_max: int = 1024, deg_min: int = 8, deg_max: int = 64):
+    """Uneven batch: per instance N log-uniform in [n_min, n_max], range width
+    log-uniform in [w_min, w_max] (values 0..width-1), alternating dense / sparse
+    (degree U{deg_min..deg_max}).  Returns small spec dicts; batch_instance()
+    materialises one."""
     rng = np.random.default_rng(seed)
-    out = []
+    specs = []
     for idx in range(n_instances):
         n = int(np.exp(rng.uniform(np.log(n_min), np.log(n_max))))
         w = int(np.exp(rng.uniform(np.log(w_min), np.log(w_max))))
         dense = (idx % 2 == 0)
-        if dense:
-            iu, ju = np.triu_indices(n, k=1)
-        else:
-            deg = int(rng.integers(deg_min, deg_max + 1))
-            m = min(n * deg // 2, n * (n - 1) // 2)
-            iu, ju = random_graph_edges(rng, n, m)
-        J = rng.standard_normal(len(iu)).astype(np.float32)
-        h = rng.standard_normal(n).astype(np.float32)
-        d = rng.random(n).astype(np.float32)
-        offs, flat, coeffs = _quio_arrays(n, np.arange(n), h, np.arange(n), d, iu, ju, J)
-        out.append(_pack_arrays(n, np.zeros(n), np.full(n, w - 1), offs, flat, coeffs, "f32"))
-    return out
+        deg = int(rng.integers(deg_min, deg_max + 1))
+        specs.append({"index": idx, "n": n, "width": max(2, w), "dense": dense, "deg": deg,
+                      "seed": int(rng.integers(0, 2 ** 31))})
+    return specs
+
+
+def batch_instance(spec, as_terms: bool = False):
+    """One batch instance: fp32 J, h ~ N(0,1), J_ii ~ U[0,1], z in [0, width-1].
+    Dense instances come as {"h", "J"} (symmetric n x n matrix) unless
+    as_terms=True; sparse ones always as a term list."""
+    rng = np.random.default_rng(spec["seed"])
+    n, w = spec["n"], spec["width"]
+    lower, upper = np.zeros(n, np.int64), np.full(n, w - 1, np.int64)
+    h = rng.standard_normal(n).astype(np.float32)
+    d = rng.random(n).astype(np.float32)
+    if spec["dense"]:
+        A = rng.standard_normal((n, n)).astype(np.float32)
+        J = np.triu(A, 1)
+        J = J + J.T
+        J[np.arange(n), np.arange(n)] = d
+        if not as_terms:
+            return {"n_vars": n, "lower": lower, "upper": upper, "h": h, "J": J, "coef_type": "f32"}
+        iu, ju = np.triu_indices(n, k=1)
+        offs, flat, coeffs = _quio_arrays(n, np.arange(n), h, np.arange(n), d, iu, ju, J[iu, ju])
+        return _pack_arrays(n, lower, upper, offs, flat, coeffs, "f32")
+    m = min(n * spec["deg"] // 2, n * (n - 1) // 2)
+    iu, ju = random_graph_edges(rng, n, m)
+    Jv = rng.standard_normal(len(iu)).astype(np.float32)
+    offs, flat, coeffs = _quio_arrays(n, np.arange(n), h, np.arange(n), d, iu, ju, Jv)
+    return _pack_arrays(n, lower, upper, offs, flat, coeffs, "f32")
