@@ -265,6 +265,60 @@ sa_status sa_batch_get_info(const sa_batch* batch, sa_batch_info* info);
 void sa_batch_destroy(sa_batch* batch);
 
 /*
+ * Serving: a request loop with continuous admission.  Requests (a model and its
+ * run parameters) queue in submission order; a dispatcher thread admits them,
+ * skipping ahead past requests that do not fit yet, whenever one of the
+ * server's streams is free and the request's device bytes (its model plus its
+ * outputs, schedule and any spilled replica state) fit in budget_bytes.  Each
+ * admitted request runs sa_run on its own stream, so requests admitted while
+ * others run overlap on the device; finished requests release their memory and
+ * stream at once.  A request's results are those of sa_run with the same model
+ * and parameters, whatever else is running.
+ *
+ * sa_server_create  budget_bytes > 0; n_streams in 1..1024 (concurrent requests).
+ * sa_server_submit  copies params (and params->temperatures); trace,
+ *                   energy_trace, report and init_states must be NULL.  The model
+ *                   must stay alive until the request is finished.  A request
+ *                   larger than the whole budget fails with SA_ERR_OOM.
+ * sa_server_poll    state: SA_REQ_QUEUED, _RUNNING, _DONE, _FAILED, _CANCELLED.
+ * sa_server_wait    waits at most timeout_us (SA_ERR_TIMEOUT after that).
+ * sa_server_cancel  cancels a queued request (SA_ERR_BUSY once it runs).
+ * sa_server_result  copies the results of a finished request into host buffers
+ *                   (any may be NULL) and releases the ticket.
+ * sa_server_get_stats  counts, device bytes in use and peak, attempts, p50/p99
+ *                   latency (submission to completion) and attempts/s from the
+ *                   first submission to the last completion.
+ * sa_server_destroy cancels queued requests, waits (bounded) for running ones.
+ */
+typedef struct sa_server sa_server;
+#define SA_REQ_QUEUED 0
+#define SA_REQ_RUNNING 1
+#define SA_REQ_DONE 2
+#define SA_REQ_FAILED 3
+#define SA_REQ_CANCELLED 4
+typedef struct {
+    uint64_t budget_bytes;
+    int32_t n_streams;
+    int32_t _reserved;
+} sa_server_config;
+typedef struct {
+    int64_t completed, failed, cancelled, queued, running;
+    int64_t device_bytes_in_use, device_bytes_peak;
+    int64_t attempts;
+    double p50_latency_ms, p99_latency_ms;
+    double attempts_per_s;
+} sa_server_stats;
+sa_status sa_server_create(sa_server** out, const sa_server_config* config);
+sa_status sa_server_submit(sa_server* server, const sa_model* model, const sa_run_params* params, uint64_t* ticket);
+sa_status sa_server_poll(sa_server* server, uint64_t ticket, int32_t* state);
+sa_status sa_server_wait(sa_server* server, uint64_t ticket, int64_t timeout_us);
+sa_status sa_server_cancel(sa_server* server, uint64_t ticket);
+sa_status sa_server_result(sa_server* server, uint64_t ticket, int32_t* states, void* energies, uint64_t* accepts,
+                           double* latency_ms);
+sa_status sa_server_get_stats(sa_server* server, sa_server_stats* stats);
+void sa_server_destroy(sa_server* server);
+
+/*
  * sa_run_noalloc -- the run of sa_run for callers that must not allocate
  * device memory.  (The paper has no counterpart; this is a library service.)
  *

@@ -52,6 +52,17 @@ class sa_batch_info(C.Structure):
                 ("_reserved", C.c_int32)]
 
 
+class sa_server_config(C.Structure):
+    _fields_ = [("budget_bytes", C.c_uint64), ("n_streams", C.c_int32), ("_reserved", C.c_int32)]
+
+
+class sa_server_stats(C.Structure):
+    _fields_ = [("completed", C.c_int64), ("failed", C.c_int64), ("cancelled", C.c_int64), ("queued", C.c_int64),
+                ("running", C.c_int64), ("device_bytes_in_use", C.c_int64), ("device_bytes_peak", C.c_int64),
+                ("attempts", C.c_int64), ("p50_latency_ms", C.c_double), ("p99_latency_ms", C.c_double),
+                ("attempts_per_s", C.c_double)]
+
+
 class sa_run_params(C.Structure):
     _fields_ = [("rule", C.c_int32), ("n_sweeps", C.c_int32), ("n_replicas", C.c_int32),
                 ("refresh_interval", C.c_int32), ("seed", C.c_uint64), ("t_max", C.c_double),
@@ -66,7 +77,9 @@ class sa_run_params(C.Structure):
 EXPORTS = ["sa_model_create", "sa_model_destroy", "sa_model_get_info", "sa_default_temperatures",
            "sa_run", "sa_energy", "sa_last_error", "sa_version", "sa_run_noalloc", "sa_model_create_quio_dense",
            "sa_batch_create", "sa_batch_autotune", "sa_batch_run", "sa_batch_result", "sa_batch_get_info",
-           "sa_batch_destroy"]
+           "sa_batch_destroy", "sa_server_create", "sa_server_submit", "sa_server_poll", "sa_server_wait",
+           "sa_server_cancel", "sa_server_result", "sa_server_get_stats", "sa_server_destroy"]
+SA_REQ_QUEUED, SA_REQ_RUNNING, SA_REQ_DONE, SA_REQ_FAILED, SA_REQ_CANCELLED = range(5)
 # size of the fixed device scratch array behind sa_run_noalloc (SA_NOALLOC_SCRATCH_BYTES)
 NOALLOC_SCRATCH_BYTES = 4 << 20
 
@@ -108,6 +121,22 @@ def load():
         lib.sa_batch_get_info.restype = C.c_int
         lib.sa_batch_destroy.argtypes = [P]
         lib.sa_batch_destroy.restype = None
+        lib.sa_server_create.argtypes = [C.POINTER(C.c_void_p), C.POINTER(sa_server_config)]
+        lib.sa_server_create.restype = C.c_int
+        lib.sa_server_submit.argtypes = [P, P, C.POINTER(sa_run_params), C.POINTER(C.c_uint64)]
+        lib.sa_server_submit.restype = C.c_int
+        lib.sa_server_poll.argtypes = [P, C.c_uint64, C.POINTER(C.c_int32)]
+        lib.sa_server_poll.restype = C.c_int
+        lib.sa_server_wait.argtypes = [P, C.c_uint64, C.c_int64]
+        lib.sa_server_wait.restype = C.c_int
+        lib.sa_server_cancel.argtypes = [P, C.c_uint64]
+        lib.sa_server_cancel.restype = C.c_int
+        lib.sa_server_result.argtypes = [P, C.c_uint64, P, P, P, C.POINTER(C.c_double)]
+        lib.sa_server_result.restype = C.c_int
+        lib.sa_server_get_stats.argtypes = [P, C.POINTER(sa_server_stats)]
+        lib.sa_server_get_stats.restype = C.c_int
+        lib.sa_server_destroy.argtypes = [P]
+        lib.sa_server_destroy.restype = None
         lib.sa_energy.argtypes = [P, P, C.c_int64, P, P]
         lib.sa_energy.restype = C.c_int
         lib.sa_last_error.argtypes = []
@@ -262,3 +291,47 @@ def sa_batch_get_info(b) -> dict:
 def sa_batch_destroy(b):
     if b:
         load().sa_batch_destroy(b)
+
+
+def sa_server_create(budget_bytes, n_streams=16):
+    cfg = sa_server_config(int(budget_bytes), int(n_streams), 0)
+    out = C.c_void_p()
+    _check(load().sa_server_create(C.byref(out), C.byref(cfg)))
+    return out.value
+
+
+def sa_server_submit(srv, model_handle, params: sa_run_params):
+    t = C.c_uint64()
+    _check(load().sa_server_submit(srv, model_handle, C.byref(params), C.byref(t)))
+    return t.value
+
+
+def sa_server_poll(srv, ticket):
+    st = C.c_int32()
+    _check(load().sa_server_poll(srv, C.c_uint64(ticket), C.byref(st)))
+    return st.value
+
+
+def sa_server_wait(srv, ticket, timeout_us):
+    _check(load().sa_server_wait(srv, C.c_uint64(ticket), int(timeout_us)))
+
+
+def sa_server_cancel(srv, ticket):
+    _check(load().sa_server_cancel(srv, C.c_uint64(ticket)))
+
+
+def sa_server_result(srv, ticket, states=None, energies=None, accepts=None):
+    lat = C.c_double()
+    _check(load().sa_server_result(srv, C.c_uint64(ticket), ptr(states), ptr(energies), ptr(accepts), C.byref(lat)))
+    return lat.value
+
+
+def sa_server_get_stats(srv) -> dict:
+    st = sa_server_stats()
+    _check(load().sa_server_get_stats(srv, C.byref(st)))
+    return {f: getattr(st, f) for f, _ in st._fields_}
+
+
+def sa_server_destroy(srv):
+    if srv:
+        load().sa_server_destroy(srv)

@@ -978,6 +978,9 @@ __attribute__((visibility("hidden"))) int sa_internal_model_view(const sa_model*
     return 1;
 }
 
+// Device bytes held by a model.
+__attribute__((visibility("hidden"))) int64_t sa_internal_model_bytes(const sa_model* M) { return M ? (int64_t)M->dbytes : 0; }
+
 // Records a failure message for sa_last_error() from another translation unit.
 __attribute__((visibility("hidden"))) void sa_internal_set_error(const char* msg) { g_last_error = msg ? msg : ""; }
 

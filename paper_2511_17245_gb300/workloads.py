@@ -321,3 +321,82 @@ def batch_instance(spec, as_terms: bool = False):
     Jv = rng.standard_normal(len(iu)).astype(np.float32)
     offs, flat, coeffs = _quio_arrays(n, np.arange(n), h, np.arange(n), d, iu, ju, Jv)
     return _pack_arrays(n, lower, upper, offs, flat, coeffs, "f32")
+
+
+# ---------------------------------------------------------------- serving stream
+def _zipf_rows(rng, n, size, count, zipf_s=1.1):
+    """count rows of `size` distinct variables with Zipf popularity (vectorised)."""
+    rank = rng.permutation(n)
+    p = 1.0 / np.power(rank + 1.0, zipf_s)
+    p /= p.sum()
+    rows = rng.choice(n, size=(count, size), p=p)
+    for _ in range(64):
+        srt = np.sort(rows, axis=1)
+        bad = np.any(srt[:, 1:] == srt[:, :-1], axis=1)
+        if not bad.any():
+            break
+        rows[bad] = rng.choice(n, size=(int(bad.sum()), size), p=p)
+    srt = np.sort(rows, axis=1)
+    keep = ~np.any(srt[:, 1:] == srt[:, :-1], axis=1)
+    return rows[keep]
+
+
+def serving_specs(seed: int = 4, n_requests: int = 20_000, n_min: int = 100, n_max: int = 50_000,
+                  w_min: int = 2, w_max: int = 4096, s_min: int = 100, s_max: int = 5000, replicas: int = 32):
+    """Request stream: 70% sparse QUIO (degree U{8..64}; dense when N <= 4096 with
+    probability 0.1), 30% HUIO with the Zipf structure of huio_zipf scaled to N;
+    N, range width and sweep count log-uniform; rule uniform; coefficients half
+    int32 U{-5..5}, half fp32 N(0,1); 32 replicas."""
+    rng = np.random.default_rng(seed)
+    rules = ["metropolis", "heat_bath", "opt_metropolis"]
+    out = []
+    for i in range(n_requests):
+        n = int(np.exp(rng.uniform(np.log(n_min), np.log(n_max))))
+        w = int(np.exp(rng.uniform(np.log(w_min), np.log(w_max))))
+        s = int(np.exp(rng.uniform(np.log(s_min), np.log(s_max))))
+        huio = rng.random() < 0.3
+        dense = (not huio) and n <= 4096 and rng.random() < 0.1
+        out.append({"index": i, "n": n, "width": max(2, w), "sweeps": s, "huio": bool(huio), "dense": bool(dense),
+                    "deg": int(rng.integers(8, 65)), "rule": rules[int(rng.integers(0, 3))],
+                    "int": bool(rng.random() < 0.5), "replicas": replicas, "seed": int(rng.integers(0, 2 ** 31))})
+    return out
+
+
+def serving_instance(spec):
+    """Materialises one request's model (term list, or dense h/J for dense QUIO)."""
+    rng = np.random.default_rng(spec["seed"])
+    n, w = spec["n"], spec["width"]
+    lo = -(w // 2)
+    lower, upper = np.full(n, lo, np.int64), np.full(n, lo + w - 1, np.int64)
+    ct = "i32" if spec["int"] else "f32"
+
+    def coef(k):
+        if spec["int"]:
+            return rng.integers(-5, 6, size=k)
+        return rng.standard_normal(k).astype(np.float32)
+
+    if spec["huio"]:
+        nq, nc, n4 = 4 * n, 10 * n, 5 * n // 2
+        blocks = [_zipf_rows(rng, n, 2, nq), _zipf_rows(rng, n, 3, nc), _zipf_rows(rng, n, 4, n4)]
+        offs = [np.zeros(1, np.int64)]
+        flat, cs = [], []
+        pos = 0
+        for b in blocks:
+            k, sz = b.shape
+            offs.append(pos + sz * np.arange(1, k + 1, dtype=np.int64))
+            pos += k * sz
+            flat.append(b.reshape(-1).astype(np.int32))
+            cs.append(coef(k))
+        return _pack_arrays(n, lower, upper, np.concatenate(offs), np.concatenate(flat), np.concatenate(cs), ct)
+    h = coef(n)
+    d = rng.integers(0, 6, size=n) if spec["int"] else rng.random(n).astype(np.float32)
+    if spec["dense"]:
+        iu, ju = np.triu_indices(n, k=1)
+        J = np.zeros((n, n), np.int32 if spec["int"] else np.float32)
+        J[iu, ju] = coef(len(iu))
+        J[np.arange(n), np.arange(n)] = d
+        return {"n_vars": n, "lower": lower, "upper": upper, "h": h, "J": J, "coef_type": ct}
+    mdeg = min(n * spec["deg"] // 2, n * (n - 1) // 2)
+    iu, ju = random_graph_edges(rng, n, mdeg)
+    offs, flat, coeffs = _quio_arrays(n, np.arange(n), h, np.arange(n), d, iu, ju, coef(len(iu)))
+    return _pack_arrays(n, lower, upper, offs, flat, coeffs, ct)

@@ -1,0 +1,130 @@
+"""Serving: requests admitted continuously under a device-memory budget.
+
+Each request's result must be the same alone and in the mix: bit-identical
+for integer models; for float models energies within 1e-5 of an FP64
+recomputation and final-energy distributions KS-compatible (p > 0.01).
+"""
+import numpy as np
+import pytest
+from scipy import stats
+
+torch = pytest.importorskip("torch")
+
+from paper_2511_17245_gb300 import (Model, SAError, make_params, sa_server_cancel, sa_server_create,
+                                    sa_server_destroy, sa_server_get_stats, sa_server_poll, sa_server_result,
+                                    sa_server_submit, sa_server_wait)
+from paper_2511_17245_gb300 import _lib
+from paper_2511_17245_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def _small_specs(seed, k):
+    specs = wl.serving_specs(seed, n_requests=k, n_min=40, n_max=1500, w_min=2, w_max=300, s_min=20, s_max=200)
+    return specs
+
+
+def _params(m, spec):
+    tmax, tmin = m.default_temperatures()
+    return make_params(spec["rule"], spec["sweeps"], spec["replicas"], seed=spec["seed"], instance_id=spec["index"],
+                       t_max=tmax, t_min=tmin)
+
+
+def _collect(srv, tickets, models, specs):
+    out = {}
+    for key, t in tickets.items():
+        sa_server_wait(srv, t, 120_000_000)
+        m, sp = models[key], specs[key]
+        st = np.zeros((sp["replicas"], m.n), np.int32)
+        en = np.zeros(sp["replicas"], np.float64 if m.is_float else np.int64)
+        ac = np.zeros(sp["replicas"], np.uint64)
+        sa_server_result(srv, t, st, en, ac)
+        out[key] = (st, en, ac)
+    return out
+
+
+def test_alone_equals_in_mix():
+    specs = _small_specs(21, 40)
+    models = {s["index"]: Model(wl.serving_instance(s)) for s in specs}
+    byidx = {s["index"]: s for s in specs}
+    probes = [s["index"] for s in specs[:8]]
+    srv = sa_server_create(8 << 30, n_streams=16)
+    try:
+        alone = {}
+        for k in probes:
+            t = sa_server_submit(srv, models[k].handle, _params(models[k], byidx[k]))
+            alone.update(_collect(srv, {k: t}, models, byidx))
+        tickets = {k: sa_server_submit(srv, models[k].handle, _params(models[k], byidx[k])) for k in byidx}
+        mix = _collect(srv, tickets, models, byidx)
+        st = sa_server_get_stats(srv)
+        assert st["completed"] == len(probes) + len(specs) and st["failed"] == 0
+        assert st["p99_latency_ms"] >= st["p50_latency_ms"] > 0
+    finally:
+        sa_server_destroy(srv)
+    for k in probes:
+        m = models[k]
+        a, b = alone[k], mix[k]
+        if m.is_float:
+            for res in (a, b):
+                e = m.energy(torch.from_numpy(res[0]).cuda()).cpu().numpy()
+                np.testing.assert_allclose(res[1], e, rtol=1e-5, atol=1e-6)
+            assert np.array_equal(a[1], b[1]) or stats.ks_2samp(a[1], b[1]).pvalue > 0.01, k
+        else:
+            assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2]), k
+    # and equal to a direct sa_run
+    for k in probes:
+        m, sp = models[k], byidx[k]
+        if m.is_float:
+            continue
+        p = _params(m, sp)
+        one = m.run(sp["rule"], sp["sweeps"], sp["replicas"], seed=sp["seed"], instance_id=sp["index"],
+                    t_max=p.t_max, t_min=p.t_min)
+        assert np.array_equal(one["states"].cpu().numpy(), alone[k][0])
+
+
+def test_budget_admission_and_backfill():
+    specs = _small_specs(22, 30)
+    models = {s["index"]: Model(wl.serving_instance(s)) for s in specs}
+    byidx = {s["index"]: s for s in specs}
+    budget = 64 << 20     # a few requests at a time
+    srv = sa_server_create(budget, n_streams=64)
+    try:
+        tickets = {k: sa_server_submit(srv, models[k].handle, _params(models[k], byidx[k])) for k in byidx}
+        _collect(srv, tickets, models, byidx)
+        st = sa_server_get_stats(srv)
+        assert st["completed"] == len(specs)
+        assert 0 < st["device_bytes_peak"] <= budget
+        assert st["device_bytes_in_use"] == 0
+    finally:
+        sa_server_destroy(srv)
+
+
+def test_cancel_timeout_and_rejections():
+    big = wl.quio_sparse_wide(5, n=4000, n_edges=30000, lo=0, hi=255)
+    m = Model(big)
+    small = Model(wl.quio_dense_small(1))
+    srv = sa_server_create(1 << 30, n_streams=1)
+    try:
+        long_p = make_params("heat_bath", 400, 256, seed=1)
+        t_long = sa_server_submit(srv, m.handle, long_p)
+        t_q = sa_server_submit(srv, small.handle, make_params("metropolis", 10, 4, t_max=10.0, t_min=1.0))
+        assert sa_server_poll(srv, t_q) == _lib.SA_REQ_QUEUED
+        sa_server_cancel(srv, t_q)
+        assert sa_server_poll(srv, t_q) == _lib.SA_REQ_CANCELLED
+        with pytest.raises(SAError) as e:
+            sa_server_wait(srv, t_long, 1000)
+        assert e.value.status == _lib.SA_ERR_TIMEOUT
+        with pytest.raises(SAError) as e:
+            sa_server_cancel(srv, t_long)
+        assert e.value.status == _lib.SA_ERR_BUSY
+        sa_server_wait(srv, t_long, 300_000_000)
+        sa_server_result(srv, t_long)
+        with pytest.raises(SAError) as e:
+            sa_server_submit(srv, m.handle, make_params("metropolis", 10, 100000))
+        assert e.value.status == _lib.SA_ERR_OOM
+        p5 = Model(wl._pack(2, [-2, -2], [2, 2], [[0, 0, 0, 0, 0, 1]], [1], "i32"))
+        with pytest.raises(SAError) as e:
+            sa_server_submit(srv, p5.handle, make_params("opt_metropolis", 5, 2))
+        assert e.value.status == _lib.SA_ERR_UNSUPPORTED
+    finally:
+        sa_server_destroy(srv)
