@@ -37,6 +37,10 @@ WORKLOAD = "quio_sparse_wide"
 METRIC = "variable-update attempts/s"
 UNIT = "attempts/s"
 L2_FLUSH_BYTES = 512 << 20
+# DRAM bytes (read + write) of one heat-bath launch from an ncu capture of this
+# kernel (profiles/sweep_heat_bath_quio_sparse_wide.md); the model and the
+# replica state stay in L2 / shared memory, so it does not grow with sweeps.
+HB_TRAFFIC_BYTES = 2.354e6
 
 
 def _peaks():
@@ -107,6 +111,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(value, device=None):
+    """Max of a per-rank float over the process group (the job's time is the
+    slowest rank's); the value itself on a single process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------- CPU oracle leg
 def oracle_sample(inst, replicas_per_rule=64, sweeps=2, threads=None):
     """Times the oracle as it stands on the host cores: for each rule,
@@ -165,6 +181,131 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------- growth directions
+def run_batched_vs_plain(torch, sample_every=128):
+    """4,096 uneven QUIO instances (N log-uniform in [50,2000], range width
+    log-uniform in [2,1024], half dense / half sparse with degree 8..64, fp32),
+    32 replicas, 1000 sweeps, Metropolis, per-instance temperatures of
+    Sect. 3.4: one persistent graph-captured launch (autotuned shape) vs the
+    plain form (one sa_run launch per instance, serialised on one stream),
+    timed on every `sample_every`-th instance and scaled up.  Both forms use the
+    same Philox counters, so their final energies agree (same quality); the
+    time-to-target energy of each form is its time to produce those energies."""
+    import concurrent.futures as cf
+    from paper_2511_17245_gb300 import (Model, make_params, sa_batch_autotune, sa_batch_create, sa_batch_destroy,
+                                        sa_batch_get_info, sa_batch_result, sa_batch_run, sa_run)
+    from paper_2511_17245_gb300 import workloads as wl
+    specs = wl.batch_specs(3)
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        insts = list(ex.map(wl.batch_instance, specs))
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        models = list(ex.map(Model, insts))
+    create_s = time.perf_counter() - t0
+    params = []
+    for i, m in enumerate(models):
+        tmax, tmin = m.default_temperatures()
+        params.append(make_params("metropolis", 1000, 32, seed=0, instance_id=i, t_max=tmax, t_min=tmin))
+    st = torch.cuda.current_stream()
+    b = sa_batch_create([m.handle for m in models], params)
+    try:
+        sa_batch_autotune(b, 10, st.cuda_stream)
+        info = sa_batch_get_info(b)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        sa_batch_run(b, st.cuda_stream)
+        e1.record(st)
+        torch.cuda.synchronize()
+        batched_ms = e0.elapsed_time(e1)
+        # stratified: instances alternate dense / sparse, so take every
+        # sample_every-th instance of each class
+        sample = list(range(0, len(models), sample_every)) + list(range(1, len(models), sample_every))
+        plain_ms, rel = 0.0, []
+        for i in sample:
+            m, p = models[i], params[i]
+            o_s = torch.empty((32, m.n), dtype=torch.int32, device="cuda")
+            o_e = torch.empty(32, dtype=torch.float64, device="cuda")
+            e0.record(st)
+            sa_run(m.handle, p, o_s, o_e, None, st.cuda_stream)
+            e1.record(st)
+            torch.cuda.synchronize()
+            plain_ms += e0.elapsed_time(e1)
+            be = np.zeros(32, np.float64)
+            sa_batch_result(b, i, None, be, None)
+            pe = o_e.cpu().numpy()
+            rel.append(abs(be.mean() - pe.mean()) / max(1e-12, abs(pe.mean())))
+        plain_total_ms = plain_ms * len(models) / len(sample)
+        att = info["attempts"]
+        return {"workload": "4096 uneven QUIO instances, 32 replicas, 1000 sweeps, metropolis",
+                "model_create_s": create_s, "batched_ms": batched_ms, "batched_attempts_per_s": att / (batched_ms / 1e3),
+                "plain_ms_estimated": plain_total_ms, "plain_attempts_per_s": att / (plain_total_ms / 1e3),
+                "plain_sample": f"every {sample_every}th instance ({len(sample)} launches), scaled by {len(models) / len(sample):.0f}",
+                "speedup": plain_total_ms / batched_ms,
+                "time_to_target_ms": {"batched": batched_ms, "plain": plain_total_ms},
+                "final_energy_mean_rel_diff_max": float(max(rel)), "launch_shape": info}
+    finally:
+        sa_batch_destroy(b)
+
+
+def run_serving(torch, n_requests=40, load=0.8):
+    """A prefix of the request stream (N log-uniform in [100, 50,000], ranges up
+    to 4096, 70% QUIO / 30% HUIO, mixed rules, 100-5000 sweeps, int32 or fp32
+    coefficients, 32 replicas) through the server with a 150 GB device budget:
+    first all requests at once (closed loop: capacity in attempts/s), then the
+    same requests with Poisson arrivals at `load` times that capacity (latency
+    percentiles)."""
+    import concurrent.futures as cf
+    from paper_2511_17245_gb300 import (Model, make_params, sa_server_create, sa_server_destroy,
+                                        sa_server_get_stats, sa_server_result, sa_server_submit, sa_server_wait)
+    from paper_2511_17245_gb300 import workloads as wl
+    specs = wl.serving_specs(4)[:n_requests]
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        insts = list(ex.map(wl.serving_instance, specs))
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        models = list(ex.map(Model, insts))
+    create_s = time.perf_counter() - t0
+    params = []
+    for sp, m in zip(specs, models):
+        tmax, tmin = m.default_temperatures()
+        params.append(make_params(sp["rule"], sp["sweeps"], sp["replicas"], seed=sp["seed"], instance_id=sp["index"],
+                                  t_max=tmax, t_min=tmin))
+    mean_att = float(np.mean([sp["n"] * sp["replicas"] * sp["sweeps"] for sp in specs]))
+
+    def one_pass(rate):
+        rng = np.random.default_rng(7)
+        srv = sa_server_create(150 << 30, n_streams=64)
+        try:
+            tickets = []
+            start = time.perf_counter()
+            arrival = 0.0
+            for m, p in zip(models, params):
+                if rate:
+                    arrival += rng.exponential(1.0 / rate)
+                    delay = start + arrival - time.perf_counter()
+                    if delay > 0:
+                        time.sleep(delay)
+                tickets.append(sa_server_submit(srv, m.handle, p))
+            for t in tickets:
+                sa_server_wait(srv, t, 3_600_000_000)
+                sa_server_result(srv, t)
+            return sa_server_get_stats(srv)
+        finally:
+            sa_server_destroy(srv)
+
+    closed = one_pass(None)
+    rate = load * closed["attempts_per_s"] / mean_att
+    open_ = one_pass(rate)
+    return {"workload": f"first {n_requests} requests of the 20,000-request stream", "model_create_s": create_s,
+            "closed_loop": {"attempts_per_s": closed["attempts_per_s"], "p50_latency_ms": closed["p50_latency_ms"],
+                            "p99_latency_ms": closed["p99_latency_ms"]},
+            "poisson": {"arrival_rate_per_s": rate, "load": load, "attempts_per_s": open_["attempts_per_s"],
+                        "p50_latency_ms": open_["p50_latency_ms"], "p99_latency_ms": open_["p99_latency_ms"],
+                        "completed": open_["completed"], "failed": open_["failed"],
+                        "device_bytes_peak": open_["device_bytes_peak"]},
+            "budget_bytes": 150 << 30}
+
+
 # ---------------------------------------------------------------- GPU leg
 def main():
     ap = argparse.ArgumentParser()
@@ -180,6 +321,8 @@ def main():
     ap.add_argument("--replicas", type=int, default=REPLICAS,
                     help="override for profiling a smaller case (bench numbers use the default)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--extended", action="store_true",
+                    help="also run the batched-vs-plain and serving measurements (several minutes)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -251,10 +394,7 @@ def main():
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in step_events]
     total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, device="cuda")
     attempts_per_run = n * R * S
     attempts = attempts_per_run * len(rules) * args.steps * world
     value = attempts / (total_ms / 1000.0)
@@ -276,8 +416,11 @@ def main():
         achieved = work / (per_rule[dom]["ms"] / 1000.0) / 1e12
         peak = 16 * 152 * sm_max * 1e6 / 1e12
         roof = {"bound": "alu", "kernel": f"sweep_kernel<{dom}>", "achieved": achieved, "peak": peak,
-                "unit": "Texp/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": f"SFU 16/clk/SM x 152 SMs x {sm_max:.0f} MHz ({peak_kind} clock)"}
+                "unit": "Texp/s", "frac": achieved / peak, "traffic": HB_TRAFFIC_BYTES,
+                "peak_source": f"SFU 16/clk/SM x 152 SMs x {sm_max:.0f} MHz ({peak_kind} clock)",
+                "note": "algorithmic work = u-l+1 exp2 per attempt (Eq. prob_heatbath); the kernel evaluates only "
+                        "the window that carries all but e^-20 of the weight, so this is effective throughput; "
+                        "traffic = DRAM bytes per launch from ncu (profiles/sweep_heat_bath_quio_sparse_wide.md)"}
     else:
         # algorithmic bytes per attempt: read z_k (1 B) + f_k (4 B); on a change
         # write z_k (1 B) and read-modify-write deg fields (8 B each) plus the
@@ -319,6 +462,11 @@ def main():
         cpu = oracle_sample(inst, replicas_per_rule=args.ref_replicas, sweeps=1)
         cpu.pop("seconds", None)
 
+    extended = None
+    if rank == 0 and args.extended:
+        extended = {"batched_vs_plain": run_batched_vs_plain(torch)}
+        extended["serving"] = run_serving(torch)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -328,6 +476,8 @@ def main():
                 "per_rule": per_rule, "accept_rate_last_rule": acc_rate,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": len(rules) * args.steps, "clocks": clocks}
+        if extended is not None:
+            line["extended"] = extended
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

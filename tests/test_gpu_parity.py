@@ -275,3 +275,35 @@ def test_errors():
     with pytest.raises(SAError) as e:
         model.energy(torch.full((1, 2), 9, dtype=torch.int32, device="cuda"))
     assert e.value.status == 1
+
+
+# ------------------------------------------------------------------ paper models
+@pytest.mark.parametrize("rule", ALL_RULES)
+def test_multilinear_order_30(rule):
+    """E^ML_{30,1} (Sect. 4): terms of 30 distinct variables (general order)."""
+    inst = wl.multilinear(100, 30, 1, integer=True)
+    _check_int_parity(inst, rule, 200, 16, 3, 8, label="ML p=30 u=1")
+
+
+@pytest.mark.parametrize("rule", ALL_RULES)
+def test_fully_connected_u100(rule):
+    """E^FC_{2,100} (Sect. 4), integer-scaled by u^2: dense pairs, z in [-100,100]
+    (heat bath over 201 values)."""
+    inst = wl.fully_connected(100, 2, 100, integer=True)
+    S = 200 if rule != "heat_bath" else 60
+    _check_int_parity(inst, rule, S, 8, 5, 4, label="FC p=2 u=100")
+
+
+def test_energy_trace_equals_oracle():
+    """Per-sweep energies (for energy-vs-sweep curves) equal the oracle's."""
+    inst = wl.random_interaction(40, 4, 6, n_terms=300, seed=3, integer=True, int_scale=20)
+    model = Model(inst)
+    om = orc.Model(inst)
+    S, R = 50, 6
+    et = torch.zeros((S, R), dtype=torch.int64, device="cuda")
+    trace = torch.zeros((S, R, model.n), dtype=torch.int32, device="cuda")
+    model.run("heat_bath", S, R, seed=2, t_max=500.0, t_min=1.0, energy_trace=et, trace=trace, trace_replicas=R)
+    x = om.run("heat_bath", S, 2, 500.0, 1.0, r_begin=0, r_end=R, energy_trace=True, trace=trace.cpu().numpy(),
+               trace_replicas=R)
+    assert x["follow"]["mismatch"] == 0
+    assert np.array_equal(x["energy_trace"], et.cpu().numpy())
