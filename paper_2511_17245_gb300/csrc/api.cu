@@ -800,13 +800,20 @@ sa_status sa_run(const sa_model* M, const sa_run_params* p, int32_t* out_states,
         tpr = std::min(256, std::max(32, (want + 31) / 32 * 32));
     }
     if (tpr % 32 != 0 || tpr > 512) return fail(SA_ERR_INVALID, "threads_per_replica must be a multiple of 32, <= 512");
-    const int list_cap = 64;
+    // QUIO rows are cheap per entry (one atomic) and go inline up to 64 links;
+    // HUIO incidences cost a term product each and go inline up to 8
+    const bool huio = M->dm.kind == sa::KIND_HUIO;
+    const int heavy_links = huio ? 8 : 64;
+    const int list_cap = huio ? 256 : 64;
     const size_t off_z = 0;
     const size_t off_cache = align_up(off_z + (size_t)n * M->zbytes, 16);
     const size_t off_ctl = align_up(off_cache + (size_t)M->cache_elems * fsize, 16);
     const size_t off_list = off_ctl + 16;
-    const size_t off_red = align_up(off_list + (size_t)list_cap * 12, 16);
-    const size_t rep_bytes = align_up(off_red + (size_t)(tpr / 32) * 8, 16);
+    const size_t off_red = align_up(off_list + (size_t)list_cap * 24, 16);
+    const size_t lvl_bytes = (size_t)(M->n_levels + 1) * 4;
+    const bool lvl_on_chip = lvl_bytes <= 16384;
+    const size_t off_lvl = align_up(off_red + (size_t)(tpr / 32) * 8, 16);
+    const size_t rep_bytes = align_up(off_lvl + (lvl_on_chip ? lvl_bytes : 0), 16);
     const int smem_max = sa::sweep_max_shared_optin();
     int fit = (int)((size_t)smem_max / rep_bytes);
     fit = std::min(fit, std::min(15, 512 / tpr));
@@ -879,9 +886,10 @@ sa_status sa_run(const sa_model* M, const sa_run_params* p, int32_t* out_states,
     a.off_ctl = (int32_t)off_ctl;
     a.off_list = (int32_t)off_list;
     a.off_red = (int32_t)off_red;
+    a.off_lvl = lvl_on_chip ? (int32_t)off_lvl : -1;
     a.rpc = rpc;
     a.tpr = tpr;
-    a.heavy_links = 64;
+    a.heavy_links = heavy_links;
     a.list_cap = list_cap;
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;

@@ -85,8 +85,14 @@ size_t layout(sa::SweepArgs& a, const sa::ModelView& v, int zb, int tpr) {
     a.off_cache = (int32_t)up16((size_t)v.n * zb);
     a.off_ctl = (int32_t)up16((size_t)a.off_cache + (size_t)v.cache_elems * fsize);
     a.off_list = a.off_ctl + 16;
-    a.off_red = (int32_t)up16((size_t)a.off_list + (size_t)kListCap * 12);
-    const size_t rep = up16((size_t)a.off_red + (size_t)(tpr / 32) * 8);
+    const int cap = v.dm.kind == sa::KIND_HUIO ? 256 : kListCap;
+    a.list_cap = cap;
+    a.heavy_links = v.dm.kind == sa::KIND_HUIO ? 8 : 64;
+    a.off_red = (int32_t)up16((size_t)a.off_list + (size_t)cap * 24);
+    const size_t lvl_bytes = (size_t)(v.n_levels + 1) * 4;
+    const size_t off_lvl = up16((size_t)a.off_red + (size_t)(tpr / 32) * 8);
+    a.off_lvl = lvl_bytes <= 16384 ? (int32_t)off_lvl : -1;
+    const size_t rep = up16(off_lvl + (lvl_bytes <= 16384 ? lvl_bytes : 0));
     a.rep_bytes = (int64_t)rep;
     a.tpr = tpr;
     return rep;
@@ -317,8 +323,6 @@ sa_status sa_batch_create(sa_batch** out, const sa_model* const* models, int32_t
         a.energy_trace = p.energy_trace;
         a.drift_bits = nullptr;
         a.gstate = nullptr;
-        a.heavy_links = 64;
-        a.list_cap = kListCap;
         tpos += 2 * (size_t)S;
     }
     e = cudaMemcpy(d_tab, tab.data(), sizeof(float) * n_tab, cudaMemcpyHostToDevice);

@@ -132,13 +132,18 @@ extern "C" sa_status sa_run_noalloc(const sa_model* M, const sa_run_params* p, i
         tpr = std::min(256, std::max(32, (want + 31) / 32 * 32));
     }
     if (tpr % 32 != 0 || tpr > 512) return fail(SA_ERR_INVALID, "threads_per_replica must be a multiple of 32, <= 512");
-    const int list_cap = 64;
+    const bool huio = mv.dm.kind == sa::KIND_HUIO;
+    const int heavy_links = huio ? 8 : 64;
+    const int list_cap = huio ? 256 : 64;
     const size_t off_z = 0;
     const size_t off_cache = round_up(off_z + (size_t)n * mv.zbytes, 16);
     const size_t off_ctl = round_up(off_cache + (size_t)mv.cache_elems * fsize, 16);
     const size_t off_list = off_ctl + 16;
-    const size_t off_red = round_up(off_list + (size_t)list_cap * 12, 16);
-    const size_t rep_bytes = round_up(off_red + (size_t)(tpr / 32) * 8, 16);
+    const size_t off_red = round_up(off_list + (size_t)list_cap * 24, 16);
+    const size_t lvl_bytes = (size_t)(mv.n_levels + 1) * 4;
+    const bool lvl_on_chip = lvl_bytes <= 16384;
+    const size_t off_lvl = round_up(off_red + (size_t)(tpr / 32) * 8, 16);
+    const size_t rep_bytes = round_up(off_lvl + (lvl_on_chip ? lvl_bytes : 0), 16);
     int fit = (int)((size_t)sa::sweep_max_shared_optin() / rep_bytes);
     fit = std::min(fit, std::min(15, 512 / tpr));
     const bool in_global = (fit < 1) || (p->flags & SA_FLAG_STATE_IN_GLOBAL);
@@ -186,9 +191,10 @@ extern "C" sa_status sa_run_noalloc(const sa_model* M, const sa_run_params* p, i
     a.off_ctl = (int32_t)off_ctl;
     a.off_list = (int32_t)off_list;
     a.off_red = (int32_t)off_red;
+    a.off_lvl = lvl_on_chip ? (int32_t)off_lvl : -1;
     a.rpc = rpc;
     a.tpr = tpr;
-    a.heavy_links = 64;
+    a.heavy_links = heavy_links;
     a.list_cap = list_cap;
     const int le = sa::launch_sweep(a, mv.zbytes, p->rule, !in_global, blocks, rpc * tpr, shared, stream);
     if (le != 0) return fail(SA_ERR_CUDA, std::string("sweep launch: ") + cudaGetErrorString((cudaError_t)le));

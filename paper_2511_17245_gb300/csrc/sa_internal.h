@@ -100,6 +100,7 @@ struct SweepArgs {
     uint8_t* gstate;            // per-replica state slabs when not on chip
     int64_t rep_bytes;          // bytes of one replica's state region
     int32_t off_z, off_cache, off_ctl, off_list, off_red;
+    int32_t off_lvl;            // level boundaries staged in the replica region (-1: read from the model)
     int32_t rpc;                // replicas per block
     int32_t tpr;                // threads per replica (multiple of 32)
     int32_t heavy_links;        // link_len above which updates are cooperative

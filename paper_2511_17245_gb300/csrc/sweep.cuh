@@ -85,6 +85,10 @@ struct Num<float> {
     __device__ static float to_f(float v) { return v; }
 };
 
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ void named_bar(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
@@ -545,8 +549,14 @@ __device__ __forceinline__ long long heat_bath_quio_f32_small(float f, float d, 
         if (b < nrb) {
             const float a0 = dzb0 + (float)(b * 16);
             if (base + b * 16 + 15 < n) {
+                float w[16];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) acc += quio_w(a0 + (float)j, d, c1, b2, mb);
+                for (int j = 0; j < 16; ++j) w[j] = quio_w(a0 + (float)j, d, c1, b2, mb);
+#pragma unroll
+                for (int h = 8; h >= 1; h >>= 1)
+#pragma unroll
+                    for (int j = 0; j < h; ++j) w[j] += w[j + h];
+                acc = w[0];
             } else {
                 const int cnt = n - (base + b * 16);
                 for (int j = 0; j < cnt; ++j) acc += quio_w(a0 + (float)j, d, c1, b2, mb);
@@ -904,6 +914,10 @@ __device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot,
         zs[k] = (Z)off;
     }
     if (t == 0) { ctl[0] = 0; ctl[1] = 0; ctl[2] = 0; }
+    // level boundaries, staged on chip when the table is small
+    int* lvl_s = a.off_lvl >= 0 ? reinterpret_cast<int*>(base + a.off_lvl) : nullptr;
+    if (lvl_s)
+        for (int L = t; L <= m.n_levels; L += tpr) lvl_s[L] = __ldg(m.lvl_ptr + L);
     named_bar(bar_id, tpr);
 
     float drift = 0.f;
@@ -926,6 +940,7 @@ __device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot,
     }
 
     unsigned long long changes = 0;
+    float dacc = 0.f;  // float models: energy changes since the last fold into eacc
     int gl3 = 0;  // level counter mod 3: which cooperative-list counter is live
 
     // Decision for one record (reads replica state only).
@@ -983,16 +998,20 @@ __device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot,
         const int k = rc.k;
         if (v != z) {
             zs[k] = (Z)(v - (long long)rc.lo);
-            eacc += (Acc)de;
+            if constexpr (Num<F>::is_float) dacc += (float)de;   // folded into eacc at refreshes
+            else eacc += (Acc)de;
             ++changes;
             const int len = rc.link_len;
             bool inline_upd = len <= a.heavy_links;
             if (!inline_upd) {
                 const int idx = atomicAdd(cnt_now, 1);
                 if (idx < a.list_cap) {
-                    list[3 * idx + 0] = k;
-                    list[3 * idx + 1] = (int)z;
-                    list[3 * idx + 2] = (int)v;
+                    int* e = list + 6 * idx;
+                    e[0] = k;
+                    e[1] = (int)z;
+                    e[2] = (int)v;
+                    e[3] = rc.link_begin;
+                    e[4] = len;
                 } else {
                     inline_upd = true;
                 }
@@ -1015,12 +1034,13 @@ __device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot,
         return q;
     };
 
-    // records of the current level's first two items per thread, prefetched
-    // one level ahead
-    int lb = __ldg(m.lvl_ptr), le = __ldg(m.lvl_ptr + 1);
-    LevelRec ra{}, rb{};
-    if (lb + t < le) ra = load_rec(lb + t);
-    if (lb + t + tpr < le) rb = load_rec(lb + t + tpr);
+    auto lvl_at = [&](int L) -> int { return lvl_s ? lvl_s[L] : __ldg(m.lvl_ptr + L); };
+    // prefetch into L1 the records this thread will read in level L
+    auto prefetch_level = [&](int L) {
+        const int b0 = lvl_at(L), b1 = lvl_at(L + 1);
+        for (int i = b0 + t; i < b1; i += tpr) prefetch_l1(m.lvl_rec + i);
+    };
+    prefetch_level(0);
 
     for (int s = 0; s < a.S; ++s) {
         const float beta = __ldg(a.beta + s);
@@ -1028,29 +1048,12 @@ __device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot,
         for (int L = 0; L < m.n_levels; ++L) {
             int* cnt_now = ctl + gl3;
             if (t == 0) ctl[gl3 == 2 ? 0 : gl3 + 1] = 0;
-            // prefetch the next level (the first level of the next sweep after the last)
-            int Ln = L + 1;
-            bool more = true;
-            if (Ln == m.n_levels) {
-                Ln = 0;
-                more = (s + 1 < a.S);
-            }
-            int lbn = 0, len = 0;
-            LevelRec na{}, nb{};
-            bool vna = false, vnb = false;
-            if (more) {
-                lbn = __ldg(m.lvl_ptr + Ln);
-                len = __ldg(m.lvl_ptr + Ln + 1);
-                vna = lbn + t < len;
-                vnb = lbn + t + tpr < len;
-                if (vna) na = load_rec(lbn + t);
-                if (vnb) nb = load_rec(lbn + t + tpr);
-            }
-            // one call site: the first two items use the prefetched records
-            for (int j = 0;; ++j) {
-                const int i = lb + t + j * tpr;
-                if (i >= le) break;
-                const LevelRec rc = (j == 0) ? ra : ((j == 1) ? rb : load_rec(i));
+            const int lb = lvl_at(L), le = lvl_at(L + 1);
+            // the next level (the first level of the next sweep after the last)
+            if (L + 1 < m.n_levels) prefetch_level(L + 1);
+            else if (s + 1 < a.S) prefetch_level(0);
+            for (int i = lb + t; i < le; i += tpr) {
+                const LevelRec rc = load_rec(i);
                 long long zz, vv2;
                 F d2;
                 decide(rc, s, beta, ratio, zz, vv2, d2);
@@ -1059,25 +1062,40 @@ __device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot,
             named_bar(bar_id, tpr);
             const int cnt = *cnt_now;
             if (cnt > 0) {
+                // cooperative updates: every thread takes the next (entry, link)
+                // pair; entry h owns links [pre_h, pre_h + len_h) of the flattened list
                 const int nl = cnt < a.list_cap ? cnt : a.list_cap;
-                for (int h = 0; h < nl; ++h) {
-                    const int k = list[3 * h + 0];
-                    const long long zold = list[3 * h + 1], znew = list[3 * h + 2];
-                    const VarMeta mt = m.meta[k];
+                int* total = ctl + 3;
+                if (t == 0) {
+                    int run = 0;
+                    for (int h = 0; h < nl; ++h) {
+                        list[6 * h + 5] = run;
+                        run += list[6 * h + 4];
+                    }
+                    *total = run;
+                }
+                named_bar(bar_id, tpr);
+                const int W = *total;
+                int h = 0;
+                for (int w = t; w < W; w += tpr) {
+                    // largest h with pre_h <= w (w only grows: continue from the last h)
+                    while (h + 1 < nl && list[6 * (h + 1) + 5] <= w) ++h;
+                    const int* ent = list + 6 * h;
+                    const int e = ent[3] + (w - ent[5]);
+                    const long long zold = ent[1], znew = ent[2];
                     if constexpr (KIND == KIND_QUIO)
-                        quio_update_range<F>(m, cache, mt.link_begin + t, mt.link_begin + mt.link_len, tpr, znew - zold);
+                        quio_update_range<F>(m, cache, e, e + 1, 1, znew - zold);
                     else
-                        huio_update_range<F, Z>(m, zs, cache, k, mt.link_begin + t, mt.link_begin + mt.link_len, tpr,
-                                                zold, znew);
+                        huio_update_range<F, Z>(m, zs, cache, ent[0], e, e + 1, 1, zold, znew);
                 }
                 named_bar(bar_id, tpr);
             }
             gl3 = gl3 == 2 ? 0 : gl3 + 1;
-            ra = na; rb = nb; lb = lbn; le = len;
-            (void)vna; (void)vnb;
         }
         // ---- FP64 refresh of float fields and energy
         if constexpr (Num<F>::is_float) {
+            eacc += (double)dacc;
+            dacc = 0.f;
             const bool last = (s + 1 == a.S);
             if (last || (a.refresh_interval > 0 && (s + 1) % a.refresh_interval == 0)) {
                 Acc f1 = 0, f2 = 0;
