@@ -504,8 +504,10 @@ __device__ long long heat_bath_general(const VarView<F, KIND>& vv, long long z, 
 // values counted from the window start (so every lane loops over its own
 // window) are summed in registers; the pick scans the block sums and
 // recomputes one block.
-__device__ __forceinline__ float quio_w(float dz, float d, float c1, float b2, float mb) {
-    return ex2_ftz(fmaf(-dz * fmaf(d, dz, c1), b2, mb));
+// weight 2^((dE_min - dE(dz)) b2), the exponent written as the polynomial
+// A dz^2 + B dz + C with A = -b2 d, B = -b2 c1, C = b2 dE_min (Horner form)
+__device__ __forceinline__ float quio_w(float dz, float A, float B, float C) {
+    return ex2_ftz(fmaf(fmaf(A, dz, B), dz, C));
 }
 
 __device__ __forceinline__ long long heat_bath_quio_f32_small(float f, float d, long long z, long long lo,
@@ -537,6 +539,7 @@ __device__ __forceinline__ long long heat_bath_quio_f32_small(float f, float d, 
         if (!(wlo <= whi)) { wlo = dz0; whi = dzn; }   // non-finite slope etc.: whole range
     }
     const float b2 = beta * 1.4426950408889634f, mb = mn * b2;
+    const float hA = -b2 * d, hB = -b2 * c1;
     const int kb0 = (int)(wlo - dz0) >> 4, kb1 = (int)(whi - dz0) >> 4;
     const int base = kb0 * 16;
     const int nrb = kb1 - kb0 + 1;
@@ -551,7 +554,7 @@ __device__ __forceinline__ long long heat_bath_quio_f32_small(float f, float d, 
             if (base + b * 16 + 15 < n) {
                 float w[16];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) w[j] = quio_w(a0 + (float)j, d, c1, b2, mb);
+                for (int j = 0; j < 16; ++j) w[j] = quio_w(a0 + (float)j, hA, hB, mb);
 #pragma unroll
                 for (int h = 8; h >= 1; h >>= 1)
 #pragma unroll
@@ -559,7 +562,7 @@ __device__ __forceinline__ long long heat_bath_quio_f32_small(float f, float d, 
                 acc = w[0];
             } else {
                 const int cnt = n - (base + b * 16);
-                for (int j = 0; j < cnt; ++j) acc += quio_w(a0 + (float)j, d, c1, b2, mb);
+                for (int j = 0; j < cnt; ++j) acc += quio_w(a0 + (float)j, hA, hB, mb);
             }
         }
         bs[b] = acc;
@@ -592,7 +595,7 @@ __device__ __forceinline__ long long heat_bath_quio_f32_small(float f, float d, 
     const int last = min(first + 15, n - 1);
     const float a0 = dz0 + (float)first;
     for (int j = 0; j <= last - first; ++j) {
-        run += quio_w(a0 + (float)j, d, c1, b2, mb);
+        run += quio_w(a0 + (float)j, hA, hB, mb);
         if (run >= thr) return lo + (long long)(first + j);
     }
     return lo + (long long)last;
@@ -994,7 +997,7 @@ __device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot,
     };
     // Applies a decision: state, energy, counters and the neighbours' caches
     // (inline for short incidence lists, else through the cooperative list).
-    auto apply = [&](const LevelRec& rc, int s, long long z, long long v, F de, int* cnt_now) {
+    auto apply = [&](const LevelRec& rc, int s, long long z, long long v, F de, int* cnt_now, bool& coop) {
         const int k = rc.k;
         if (v != z) {
             zs[k] = (Z)(v - (long long)rc.lo);
@@ -1018,7 +1021,7 @@ __device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot,
             }
             if (inline_upd) {
                 if constexpr (KIND == KIND_QUIO)
-                    quio_update_row<F>(m, cache, rc.link_begin, len, v - z);
+                    coop = true;   // the warp updates this row together (below)
                 else
                     huio_update_range<F, Z>(m, zs, cache, k, rc.link_begin, rc.link_begin + len, 1, z, v);
             }
@@ -1052,12 +1055,48 @@ __device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot,
             // the next level (the first level of the next sweep after the last)
             if (L + 1 < m.n_levels) prefetch_level(L + 1);
             else if (s + 1 < a.S) prefetch_level(0);
-            for (int i = lb + t; i < le; i += tpr) {
-                const LevelRec rc = load_rec(i);
-                long long zz, vv2;
-                F d2;
-                decide(rc, s, beta, ratio, zz, vv2, d2);
-                apply(rc, s, zz, vv2, d2, cnt_now);
+            // every thread of the group runs the same number of rounds, so that a
+            // warp can share the neighbour updates of its accepting lanes
+            const int rounds = (le - lb + tpr - 1) / tpr;
+            const int lane = t & 31;
+            for (int rd = 0; rd < rounds; ++rd) {
+                const int i = lb + t + rd * tpr;
+                bool coop = false;
+                int rb = 0, rl = 0;
+                long long rdz = 0;
+                if (i < le) {
+                    const LevelRec rc = load_rec(i);
+                    long long zz, vv2;
+                    F d2;
+                    decide(rc, s, beta, ratio, zz, vv2, d2);
+                    apply(rc, s, zz, vv2, d2, cnt_now, coop);
+                    rb = rc.link_begin;
+                    rl = rc.link_len;
+                    rdz = vv2 - zz;
+                }
+                if constexpr (KIND == KIND_QUIO) {
+                    // Sect. 3.2 update of the accepted rows, one row at a time, one
+                    // entry per lane (coalesced row reads, parallel atomics)
+                    unsigned pend = __ballot_sync(0xffffffffu, coop);
+                    if (__popc(pend) > 4) {
+                        // many accepting lanes: each updates its own row
+                        if (coop) quio_update_row<F>(m, cache, rb, rl, rdz);
+                        pend = 0;
+                    }
+                    while (pend) {
+                        const int src = __ffs(pend) - 1;
+                        pend &= pend - 1;
+                        const int b = __shfl_sync(0xffffffffu, rb, src);
+                        const int l = __shfl_sync(0xffffffffu, rl, src);
+                        const long long dz = __shfl_sync(0xffffffffu, rdz, src);
+                        for (int e = lane; e < l; e += 32) {
+                            if constexpr (Num<F>::is_float)
+                                atomic_add_field(cache + __ldg(m.adj_col + b + e), __ldg(m.adj_f + b + e) * (float)(int)dz);
+                            else
+                                atomic_add_field(cache + m.adj_col[b + e], m.adj_i[b + e] * dz);
+                        }
+                    }
+                }
             }
             named_bar(bar_id, tpr);
             const int cnt = *cnt_now;
