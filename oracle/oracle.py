@@ -130,8 +130,9 @@ class Model:
         self.upper = np.ascontiguousarray(inst["upper"], np.int64)
         offs = np.ascontiguousarray(inst["term_offsets"], np.int64)
         tv = np.ascontiguousarray(inst["term_vars"], np.int32)
-        co = np.ascontiguousarray(inst["coeffs"])
         self.coef_type = inst["coef_type"]
+        co = np.ascontiguousarray(inst["coeffs"], {"i32": np.int32, "i64": np.int64, "f32": np.float32,
+                                                   "f64": np.float64}[self.coef_type])
         h = C.c_void_p()
         rc = lib.om_model_create(C.byref(h), self.n, _ptr(self.lower), _ptr(self.upper),
                                  len(offs) - 1, _ptr(offs), _ptr(tv), _ptr(co), COEF[self.coef_type])
