@@ -84,6 +84,20 @@ def test_merging_duplicates_zero_and_constant():
     assert m.energy([1, 2, 0]) == 11 + 7 * 2
 
 
+def test_plain_list_instances_take_the_declared_coefficient_type():
+    """An instance given as Python lists (coefficients converted to the type it
+    declares) evaluates like the hand-expanded polynomial
+    E = 3 z0 z1 - 2 z1 z2^2 + z0, for every state of [-2, 2]^3."""
+    for ct in ("i32", "i64", "f32", "f64"):
+        inst = {"n_vars": 3, "lower": [-2] * 3, "upper": [2] * 3, "term_offsets": [0, 2, 5, 6],
+                "term_vars": [0, 1, 1, 2, 2, 0], "coeffs": [3, -2, 1], "coef_type": ct}
+        m = orc.Model(inst)
+        for z0 in range(-2, 3):
+            for z1 in range(-2, 3):
+                for z2 in range(-2, 3):
+                    assert m.energy([z0, z1, z2]) == 3 * z0 * z1 - 2 * z1 * z2 * z2 + z0, (ct, z0, z1, z2)
+
+
 def test_fully_connected_ground_energy_closed_form():
     """E^FC ground -N(N+1)/2 (Sect. 4): brute force on a tiny instance and the
     value -5050 the paper quotes for N=100, p=2, u=100 at z = u."""
