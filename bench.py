@@ -312,6 +312,45 @@ def run_serving(torch, n_requests=40, load=0.8, max_attempts=2e8):
             "budget_bytes": 150 << 30}
 
 
+def run_small_configs(torch, steps=3, warmup=3):
+    """The two other single-run workloads, each rule timed with CUDA events
+    (median of `steps` runs after `warmup`): the dense 32-variable integer QUIO
+    (z in [-8,7], 64 replicas x 1000 sweeps, T 100 -> 0.1) and the Zipf HUIO
+    (N = 2,000, z in [-50,50], 8k/20k/5k quadratic/cubic/quartic terms, int32,
+    256 replicas x 2000 sweeps, temperatures of Sect. 3.4).  Both fit in L2 and
+    shared memory; attempts/s and ns per sweep are reported."""
+    from paper_2511_17245_gb300 import Model, make_params, sa_run
+    from paper_2511_17245_gb300 import workloads as wl
+    st = torch.cuda.current_stream()
+    out = {}
+    for name, inst, R, S, temps in [("quio_dense_small", wl.quio_dense_small(0), 64, 1000, (100.0, 0.1)),
+                                    ("huio_zipf", wl.huio_zipf(2), 256, 2000, None)]:
+        m = Model(inst)
+        tmax, tmin = temps if temps else m.default_temperatures()
+        n = m.n
+        states = torch.empty((R, n), dtype=torch.int32, device="cuda")
+        energies = torch.empty(R, dtype=torch.int64, device="cuda")
+        res = {}
+        for rule in RULES:
+            p = make_params(rule, S, R, seed=0, t_max=tmax, t_min=tmin)
+            for _ in range(warmup):
+                sa_run(m.handle, p, states, energies, None, st.cuda_stream)
+            ms = []
+            for _ in range(steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                sa_run(m.handle, p, states, energies, None, st.cuda_stream)
+                e1.record(st)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            t = float(np.median(ms))
+            res[rule] = {"ms": t, "attempts_per_s": n * R * S / (t / 1e3), "us_per_sweep": 1e3 * t / S,
+                         "mean_final_energy": float(energies.double().mean().item())}
+        out[name] = {"n": n, "replicas": R, "sweeps": S, "rules": res}
+        m.close()
+    return out
+
+
 # ---------------------------------------------------------------- GPU leg
 def main():
     ap = argparse.ArgumentParser()
@@ -327,6 +366,8 @@ def main():
     ap.add_argument("--replicas", type=int, default=REPLICAS,
                     help="override for profiling a smaller case (bench numbers use the default)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--small-configs", action="store_true",
+                    help="also time the dense 32-variable QUIO and the Zipf HUIO workloads")
     ap.add_argument("--extended", action="store_true",
                     help="also run the batched-vs-plain and serving measurements (several minutes)")
     args = ap.parse_args()
@@ -468,6 +509,11 @@ def main():
         cpu = oracle_sample(inst, replicas_per_rule=args.ref_replicas, sweeps=1)
         cpu.pop("seconds", None)
 
+    small = None
+    if rank == 0 and args.small_configs:
+        small = run_small_configs(torch)
+        print(json.dumps({"small_configs": small}), file=sys.stderr, flush=True)
+
     extended = None
     if rank == 0 and args.extended:
         # each part is also written to stderr as soon as it ends
@@ -485,6 +531,8 @@ def main():
                 "per_rule": per_rule, "accept_rate_last_rule": acc_rate,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": len(rules) * args.steps, "clocks": clocks}
+        if small is not None:
+            line["small_configs"] = small
         if extended is not None:
             line["extended"] = extended
         print(json.dumps(line), flush=True)
