@@ -40,7 +40,7 @@ L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) of one heat-bath launch from an ncu capture of this
 # kernel (profiles/sweep_heat_bath_quio_sparse_wide.md); the model and the
 # replica state stay in L2 / shared memory, so it does not grow with sweeps.
-HB_TRAFFIC_BYTES = 2.320e6
+HB_TRAFFIC_BYTES = 2.757e6
 
 
 def _peaks():

@@ -1059,6 +1059,7 @@ __device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot,
             // warp can share the neighbour updates of its accepting lanes
             const int rounds = (le - lb + tpr - 1) / tpr;
             const int lane = t & 31;
+            const bool solo = le - lb == 1;
             for (int rd = 0; rd < rounds; ++rd) {
                 const int i = lb + t + rd * tpr;
                 bool coop = false;
@@ -1089,11 +1090,22 @@ __device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot,
                         const int b = __shfl_sync(0xffffffffu, rb, src);
                         const int l = __shfl_sync(0xffffffffu, rl, src);
                         const long long dz = __shfl_sync(0xffffffffu, rdz, src);
-                        for (int e = lane; e < l; e += 32) {
-                            if constexpr (Num<F>::is_float)
-                                atomic_add_field(cache + __ldg(m.adj_col + b + e), __ldg(m.adj_f + b + e) * (float)(int)dz);
-                            else
-                                atomic_add_field(cache + m.adj_col[b + e], m.adj_i[b + e] * dz);
+                        if (solo) {
+                            // the level's only variable: its row's columns are
+                            // distinct and nothing else touches the cache now
+                            for (int e = lane; e < l; e += 32) {
+                                if constexpr (Num<F>::is_float)
+                                    cache[__ldg(m.adj_col + b + e)] += __ldg(m.adj_f + b + e) * (float)(int)dz;
+                                else
+                                    cache[m.adj_col[b + e]] += m.adj_i[b + e] * dz;
+                            }
+                        } else {
+                            for (int e = lane; e < l; e += 32) {
+                                if constexpr (Num<F>::is_float)
+                                    atomic_add_field(cache + __ldg(m.adj_col + b + e), __ldg(m.adj_f + b + e) * (float)(int)dz);
+                                else
+                                    atomic_add_field(cache + m.adj_col[b + e], m.adj_i[b + e] * dz);
+                            }
                         }
                     }
                 }
@@ -1122,10 +1134,18 @@ __device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot,
                     const int* ent = list + 6 * h;
                     const int e = ent[3] + (w - ent[5]);
                     const long long zold = ent[1], znew = ent[2];
-                    if constexpr (KIND == KIND_QUIO)
-                        quio_update_range<F>(m, cache, e, e + 1, 1, znew - zold);
-                    else
+                    if constexpr (KIND == KIND_QUIO) {
+                        if (solo) {   // one row, distinct columns: no atomics needed
+                            if constexpr (Num<F>::is_float)
+                                cache[m.adj_col[e]] += __ldg(m.adj_f + e) * (float)(int)(znew - zold);
+                            else
+                                cache[m.adj_col[e]] += m.adj_i[e] * (znew - zold);
+                        } else {
+                            quio_update_range<F>(m, cache, e, e + 1, 1, znew - zold);
+                        }
+                    } else {
                         huio_update_range<F, Z>(m, zs, cache, ent[0], e, e + 1, 1, zold, znew);
+                    }
                 }
                 named_bar(bar_id, tpr);
             }
