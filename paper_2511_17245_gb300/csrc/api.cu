@@ -804,6 +804,8 @@ sa_status sa_run(const sa_model* M, const sa_run_params* p, int32_t* out_states,
     // HUIO incidences cost a term product each and go inline up to 8
     const bool huio = M->dm.kind == sa::KIND_HUIO;
     const int heavy_links = huio ? 8 : 64;
+    if (p->threads_per_replica <= 0)
+        tpr = sa::grow_threads_per_replica(tpr, M->max_link_len, heavy_links, R, p->replicas_per_block, dev_sms);
     const int list_cap = huio ? 256 : 64;
     const size_t off_z = 0;
     const size_t off_cache = align_up(off_z + (size_t)n * M->zbytes, 16);
@@ -981,6 +983,7 @@ __attribute__((visibility("hidden"))) int sa_internal_model_view(const sa_model*
     v->zbytes = M->zbytes;
     v->cache_elems = M->cache_elems;
     v->n_levels = M->n_levels;
+    v->max_link_len = M->max_link_len;
     v->de_max = M->de_max;
     v->de_min = M->de_min;
     return 1;

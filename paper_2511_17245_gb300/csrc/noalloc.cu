@@ -134,6 +134,8 @@ extern "C" sa_status sa_run_noalloc(const sa_model* M, const sa_run_params* p, i
     if (tpr % 32 != 0 || tpr > 512) return fail(SA_ERR_INVALID, "threads_per_replica must be a multiple of 32, <= 512");
     const bool huio = mv.dm.kind == sa::KIND_HUIO;
     const int heavy_links = huio ? 8 : 64;
+    if (p->threads_per_replica <= 0)
+        tpr = sa::grow_threads_per_replica(tpr, mv.max_link_len, heavy_links, R, p->replicas_per_block, sms);
     const int list_cap = huio ? 256 : 64;
     const size_t off_z = 0;
     const size_t off_cache = round_up(off_z + (size_t)n * mv.zbytes, 16);

@@ -143,8 +143,24 @@ struct ModelView {
     int zbytes;
     int64_t cache_elems;
     int32_t n_levels;
+    int32_t max_link_len;       // longest neighbour / incidence list
     double de_max, de_min;
 };
+
+// Threads per replica for a launch whose caller left the choice to the library.
+// `tpr` is the choice from the level widths; when the block's replicas leave
+// thread slots unused (few replicas per SM) and some variable's update list is
+// longer than `heavy_links` (the lists the whole group updates together), the
+// spare slots go to the replicas.  Integer results do not depend on the shape.
+inline int grow_threads_per_replica(int tpr, int32_t max_link_len, int heavy_links, int replicas,
+                                    int replicas_per_block, int sms) {
+    if (max_link_len <= heavy_links) return tpr;
+    int per_block = replicas_per_block > 0 ? replicas_per_block : (replicas + sms - 1) / (sms > 0 ? sms : 1);
+    per_block = per_block < 1 ? 1 : (per_block > 15 ? 15 : per_block);
+    int grown = (512 / per_block) / 32 * 32;
+    if (grown > 256) grown = 256;
+    return grown > tpr ? grown : tpr;
+}
 
 // Host-side launchers implemented in the .cu files.
 // zbytes in {1,2,4}; returns a cudaError_t as int.
