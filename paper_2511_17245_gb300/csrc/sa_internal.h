@@ -1,5 +1,6 @@
 // sa_internal.h -- device model layout and kernel arguments shared by the
-// host-side model compiler (model.cpp, api.cpp) and the CUDA kernels.
+// host-side model compiler and launchers (api.cu, batch.cu, noalloc.cu,
+// server.cu) and the CUDA kernels.
 #pragma once
 
 #include <cstddef>
