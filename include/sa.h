@@ -343,9 +343,12 @@ void sa_server_destroy(sa_server* server);
  *     work overlaps on the GPU (other streams, or a new call before the last
  *     one finished on another stream) race on the array and must be serialised
  *     by the caller.
- *   - The first call on each device looks up the array's device address (with
- *     that device current) and caches it; make that first call before any
- *     stream capture.
+ *   - The first call on each device does a one-time set-up: with that device
+ *     current it looks up the array's device address and caches it.  Make
+ *     that first call before any stream capture.  The cached address belongs
+ *     to the context that was current at the first call; a program that
+ *     destroys that context (cudaDeviceReset) must not call sa_run_noalloc on
+ *     that device afterwards.
  */
 #define SA_NOALLOC_SCRATCH_BYTES (4u << 20)
 sa_status sa_run_noalloc(const sa_model* model, const sa_run_params* params, int32_t* out_states,

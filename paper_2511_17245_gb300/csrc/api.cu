@@ -618,6 +618,8 @@ struct Temps {
 
 extern "C" {
 
+__attribute__((visibility("hidden"))) int sa_internal_model_view(const sa_model* M, sa::ModelView* v);
+
 sa_status sa_model_create(sa_model** out, int32_t n_vars, const int64_t* lower, const int64_t* upper,
                           int64_t n_terms, const int64_t* term_offsets, const int32_t* term_vars, const void* coeffs,
                           sa_coef_type coef_type) {
@@ -770,65 +772,22 @@ sa_status sa_run(const sa_model* M, const sa_run_params* p, int32_t* out_states,
 
     // ---- schedule (Sect. 3.1) and OTM ratio (Sect. 3.3.3)
     std::vector<float> tab(2 * (size_t)S);
-    double tmax = p->t_max, tmin = p->t_min;
-    if (!p->temperatures) {
-        if (tmax <= 0 && tmin <= 0) sa_default_temperatures(M, &tmax, &tmin);
-        else if (!(tmax > 0 && tmin > 0) || !std::isfinite(tmax) || !std::isfinite(tmin))
-            return fail(SA_ERR_INVALID, "t_max and t_min must both be positive (or both <= 0 for defaults)");
-    }
-    for (int32_t s = 0; s < S; ++s) {
-        double T;
-        if (p->temperatures) {
-            T = p->temperatures[s];
-            if (!(T > 0) || !std::isfinite(T)) return fail(SA_ERR_INVALID, "temperatures must be positive");
-        } else {
-            const double frac = S > 1 ? (double)s / (double)(S - 1) : 0.0;
-            T = tmax * std::pow(tmin / tmax, frac);
-        }
-        tab[s] = (float)(1.0 / T);
-        tab[S + s] = S > 1 ? (float)s / (float)(S - 1) : 0.0f;
-    }
+    if (const char* err = sa::plan_schedule(M->de_max, M->de_min, S, p->t_max, p->t_min, p->temperatures, tab.data()))
+        return fail(SA_ERR_INVALID, err);
 
-    // ---- launch shape
-    const size_t fsize = M->is_float ? 4 : 8;
+    // ---- launch shape and per-replica state layout
+    sa::ModelView view;
+    sa_internal_model_view(M, &view);
     int dev_sms = 0;
     cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, dev);
-    const double mean_w = (double)n / (double)std::max(1, M->n_levels);
-    int tpr = p->threads_per_replica;
-    if (tpr <= 0) {
-        int want = (int)std::ceil(mean_w / 2.0);
-        tpr = std::min(256, std::max(32, (want + 31) / 32 * 32));
-    }
-    if (tpr % 32 != 0 || tpr > 512) return fail(SA_ERR_INVALID, "threads_per_replica must be a multiple of 32, <= 512");
-    // QUIO rows are cheap per entry (one atomic) and go inline up to 64 links;
-    // HUIO incidences cost a term product each and go inline up to 8
-    const bool huio = M->dm.kind == sa::KIND_HUIO;
-    const int heavy_links = huio ? 8 : 64;
-    if (p->threads_per_replica <= 0)
-        tpr = sa::grow_threads_per_replica(tpr, M->max_link_len, heavy_links, R, p->replicas_per_block, dev_sms);
-    const int list_cap = huio ? 256 : 64;
-    const size_t off_z = 0;
-    const size_t off_cache = align_up(off_z + (size_t)n * M->zbytes, 16);
-    const size_t off_ctl = align_up(off_cache + (size_t)M->cache_elems * fsize, 16);
-    const size_t off_list = off_ctl + 16;
-    const size_t off_red = align_up(off_list + (size_t)list_cap * 24, 16);
-    const size_t lvl_bytes = (size_t)(M->n_levels + 1) * 4;
-    const bool lvl_on_chip = lvl_bytes <= 16384;
-    const size_t off_lvl = align_up(off_red + (size_t)(tpr / 32) * 8, 16);
-    const size_t rep_bytes = align_up(off_lvl + (lvl_on_chip ? lvl_bytes : 0), 16);
-    const int smem_max = sa::sweep_max_shared_optin();
-    int fit = (int)((size_t)smem_max / rep_bytes);
-    fit = std::min(fit, std::min(15, 512 / tpr));
-    bool in_global = (fit < 1) || (p->flags & SA_FLAG_STATE_IN_GLOBAL);
-    int rpc = p->replicas_per_block;
-    if (rpc <= 0) {
-        const int target = std::max(1, (R + dev_sms - 1) / std::max(1, dev_sms));
-        rpc = in_global ? std::min(target, std::min(15, 512 / tpr)) : std::min(fit, target);
-    }
-    if (rpc < 1 || rpc > 15 || rpc * tpr > 512) return fail(SA_ERR_INVALID, "replicas_per_block out of range");
-    if (!in_global && rpc > fit) return fail(SA_ERR_INVALID, "replicas_per_block exceeds shared memory");
-    const int blocks = (R + rpc - 1) / rpc;
-    const size_t shared = in_global ? 0 : (size_t)rpc * rep_bytes;
+    sa::RunPlan plan{};
+    if (const char* err = sa::plan_run_shape(sa::plan_model(view), R, p->threads_per_replica, p->replicas_per_block,
+                                             (p->flags & SA_FLAG_STATE_IN_GLOBAL) != 0, dev_sms,
+                                             sa::sweep_max_shared_optin(), &plan))
+        return fail(SA_ERR_INVALID, err);
+    const bool in_global = plan.in_global != 0;
+    const int rpc = plan.rpc, tpr = plan.tpr, blocks = plan.blocks;
+    const size_t rep_bytes = (size_t)plan.rep_bytes, shared = (size_t)plan.shared_bytes;
 
     // ---- device temporaries and host/device outputs
     Temps tmp(st);
@@ -882,17 +841,7 @@ sa_status sa_run(const sa_model* M, const sa_run_params* p, int32_t* out_states,
     a.energy_trace = p->energy_trace;
     a.drift_bits = d_drift;
     a.gstate = gstate;
-    a.rep_bytes = (int64_t)rep_bytes;
-    a.off_z = (int32_t)off_z;
-    a.off_cache = (int32_t)off_cache;
-    a.off_ctl = (int32_t)off_ctl;
-    a.off_list = (int32_t)off_list;
-    a.off_red = (int32_t)off_red;
-    a.off_lvl = lvl_on_chip ? (int32_t)off_lvl : -1;
-    a.rpc = rpc;
-    a.tpr = tpr;
-    a.heavy_links = heavy_links;
-    a.list_cap = list_cap;
+    sa::plan_apply(plan, a);
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (p->report) {

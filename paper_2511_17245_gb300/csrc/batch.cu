@@ -32,7 +32,6 @@ sa_status bfail(sa_status st, const std::string& msg) {
 sa_status bcuda(cudaError_t e, const char* where) {
     return bfail(e == cudaErrorMemoryAllocation ? SA_ERR_OOM : SA_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
-size_t up16(size_t x) { return (x + 15) / 16 * 16; }
 size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 bool dev_ptr(const void* p) {
     if (!p) return false;
@@ -76,26 +75,14 @@ struct sa_batch {
 
 namespace {
 
-const int kListCap = 64;
-
-// per-instance state layout for a given threads-per-replica
+// Per-instance state layout for a given threads-per-replica: the layout of
+// sa_run (shared planner) with the batch's widest state offsets.
 size_t layout(sa::SweepArgs& a, const sa::ModelView& v, int zb, int tpr) {
-    const size_t fsize = v.is_float ? 4 : 8;
-    a.off_z = 0;
-    a.off_cache = (int32_t)up16((size_t)v.n * zb);
-    a.off_ctl = (int32_t)up16((size_t)a.off_cache + (size_t)v.cache_elems * fsize);
-    a.off_list = a.off_ctl + 16;
-    const int cap = v.dm.kind == sa::KIND_HUIO ? 256 : kListCap;
-    a.list_cap = cap;
-    a.heavy_links = v.dm.kind == sa::KIND_HUIO ? 8 : 64;
-    a.off_red = (int32_t)up16((size_t)a.off_list + (size_t)cap * 24);
-    const size_t lvl_bytes = (size_t)(v.n_levels + 1) * 4;
-    const size_t off_lvl = up16((size_t)a.off_red + (size_t)(tpr / 32) * 8);
-    a.off_lvl = lvl_bytes <= 16384 ? (int32_t)off_lvl : -1;
-    const size_t rep = up16(off_lvl + (lvl_bytes <= 16384 ? lvl_bytes : 0));
-    a.rep_bytes = (int64_t)rep;
-    a.tpr = tpr;
-    return rep;
+    sa::RunPlan pl{};
+    const int64_t rep = sa::plan_layout(sa::plan_model(v), zb, tpr, &pl);
+    pl.rpc = a.rpc;
+    sa::plan_apply(pl, a);
+    return (size_t)rep;
 }
 
 // Sets the launch shape and rebuilds the per-instance arguments for it.
@@ -280,28 +267,11 @@ sa_status sa_batch_create(sa_batch** out, const sa_model* const* models, int32_t
         const sa_run_params& p = params[i];
         const sa::ModelView& v = b->views[i];
         const int32_t S = b->S[i];
-        double tmax = p.t_max, tmin = p.t_min;
-        if (!p.temperatures) {
-            if (tmax <= 0 && tmin <= 0) {
-                tmax = -v.de_max / std::log(0.5);
-                tmin = -v.de_min / std::log(0.001);
-            } else if (!(tmax > 0 && tmin > 0)) {
-                cudaFree(b->dmem);
-                delete b;
-                return bfail(SA_ERR_INVALID, "t_max and t_min must both be positive (instance " + std::to_string(i) + ")");
-            }
-        }
-        for (int32_t s = 0; s < S; ++s) {
-            double T;
-            if (p.temperatures) T = p.temperatures[s];
-            else T = tmax * std::pow(tmin / tmax, S > 1 ? (double)s / (double)(S - 1) : 0.0);
-            if (!(T > 0) || !std::isfinite(T)) {
-                cudaFree(b->dmem);
-                delete b;
-                return bfail(SA_ERR_INVALID, "temperatures must be positive (instance " + std::to_string(i) + ")");
-            }
-            tab[tpos + s] = (float)(1.0 / T);
-            tab[tpos + S + s] = S > 1 ? (float)s / (float)(S - 1) : 0.0f;
+        if (const char* err = sa::plan_schedule(v.de_max, v.de_min, S, p.t_max, p.t_min, p.temperatures,
+                                                tab.data() + tpos)) {
+            cudaFree(b->dmem);
+            delete b;
+            return bfail(SA_ERR_INVALID, std::string(err) + " (instance " + std::to_string(i) + ")");
         }
         sa::SweepArgs& a = b->h_insts[i];
         a = sa::SweepArgs{};

@@ -13,7 +13,6 @@
 // until the process exits.
 #include <cuda_runtime.h>
 
-#include <cmath>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -91,78 +90,30 @@ extern "C" sa_status sa_run_noalloc(const sa_model* M, const sa_run_params* p, i
     sa_status st0 = scratch_address(dev, &scratch);
     if (st0 != SA_OK) return st0;
     cudaStream_t st = (cudaStream_t)stream;
-    const int32_t S = p->n_sweeps, R = p->n_replicas, n = mv.n;
+    const int32_t S = p->n_sweeps, R = p->n_replicas;
 
-    // temperature table: same arithmetic as sa_run (Sect. 3.1, Sect. 3.3.3)
+    // temperature table and launch shape: the planner sa_run uses (Sect. 3.1,
+    // Sect. 3.3.3), so that both entry points give identical runs
     const size_t tab_bytes = round_up(2 * (size_t)S * sizeof(float), 256);
     if (tab_bytes > (size_t)SA_NOALLOC_SCRATCH_BYTES)
         return fail(SA_ERR_UNSUPPORTED, "n_sweeps too large for the fixed scratch of sa_run_noalloc (limit " +
                                             std::to_string(SA_NOALLOC_SCRATCH_BYTES / 8) + " sweeps)");
     std::vector<float> tab(2 * (size_t)S);
-    double tmax = p->t_max, tmin = p->t_min;
-    if (!p->temperatures) {
-        if (tmax <= 0 && tmin <= 0) {
-            tmax = -mv.de_max / std::log(0.5);
-            tmin = -mv.de_min / std::log(0.001);
-        } else if (!(tmax > 0 && tmin > 0) || !std::isfinite(tmax) || !std::isfinite(tmin)) {
-            return fail(SA_ERR_INVALID, "t_max and t_min must both be positive (or both <= 0 for defaults)");
-        }
-    }
-    for (int32_t s = 0; s < S; ++s) {
-        double T;
-        if (p->temperatures) {
-            T = p->temperatures[s];
-            if (!(T > 0) || !std::isfinite(T)) return fail(SA_ERR_INVALID, "temperatures must be positive");
-        } else {
-            const double frac = S > 1 ? (double)s / (double)(S - 1) : 0.0;
-            T = tmax * std::pow(tmin / tmax, frac);
-        }
-        tab[s] = (float)(1.0 / T);
-        tab[S + s] = S > 1 ? (float)s / (float)(S - 1) : 0.0f;
-    }
-
-    // launch shape: the automatic choice of sa_run
-    const size_t fsize = mv.is_float ? 4 : 8;
+    if (const char* err = sa::plan_schedule(mv.de_max, mv.de_min, S, p->t_max, p->t_min, p->temperatures, tab.data()))
+        return fail(SA_ERR_INVALID, err);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int tpr = p->threads_per_replica;
-    if (tpr <= 0) {
-        const double mean_w = (double)n / (double)(mv.n_levels > 0 ? mv.n_levels : 1);
-        const int want = (int)std::ceil(mean_w / 2.0);
-        tpr = std::min(256, std::max(32, (want + 31) / 32 * 32));
-    }
-    if (tpr % 32 != 0 || tpr > 512) return fail(SA_ERR_INVALID, "threads_per_replica must be a multiple of 32, <= 512");
-    const bool huio = mv.dm.kind == sa::KIND_HUIO;
-    const int heavy_links = huio ? 8 : 64;
-    if (p->threads_per_replica <= 0)
-        tpr = sa::grow_threads_per_replica(tpr, mv.max_link_len, heavy_links, R, p->replicas_per_block, sms);
-    const int list_cap = huio ? 256 : 64;
-    const size_t off_z = 0;
-    const size_t off_cache = round_up(off_z + (size_t)n * mv.zbytes, 16);
-    const size_t off_ctl = round_up(off_cache + (size_t)mv.cache_elems * fsize, 16);
-    const size_t off_list = off_ctl + 16;
-    const size_t off_red = round_up(off_list + (size_t)list_cap * 24, 16);
-    const size_t lvl_bytes = (size_t)(mv.n_levels + 1) * 4;
-    const bool lvl_on_chip = lvl_bytes <= 16384;
-    const size_t off_lvl = round_up(off_red + (size_t)(tpr / 32) * 8, 16);
-    const size_t rep_bytes = round_up(off_lvl + (lvl_on_chip ? lvl_bytes : 0), 16);
-    int fit = (int)((size_t)sa::sweep_max_shared_optin() / rep_bytes);
-    fit = std::min(fit, std::min(15, 512 / tpr));
-    const bool in_global = (fit < 1) || (p->flags & SA_FLAG_STATE_IN_GLOBAL);
-    int rpc = p->replicas_per_block;
-    if (rpc <= 0) {
-        const int target = std::max(1, (R + sms - 1) / std::max(1, sms));
-        rpc = in_global ? std::min(target, std::min(15, 512 / tpr)) : std::min(fit, target);
-    }
-    if (rpc < 1 || rpc > 15 || rpc * tpr > 512) return fail(SA_ERR_INVALID, "replicas_per_block out of range");
-    if (!in_global && rpc > fit) return fail(SA_ERR_INVALID, "replicas_per_block exceeds shared memory");
-    const size_t slab_bytes = in_global ? (size_t)R * rep_bytes : 0;
+    sa::RunPlan plan{};
+    if (const char* err = sa::plan_run_shape(sa::plan_model(mv), R, p->threads_per_replica, p->replicas_per_block,
+                                             (p->flags & SA_FLAG_STATE_IN_GLOBAL) != 0, sms,
+                                             sa::sweep_max_shared_optin(), &plan))
+        return fail(SA_ERR_INVALID, err);
+    const bool in_global = plan.in_global != 0;
+    const size_t slab_bytes = in_global ? (size_t)R * (size_t)plan.rep_bytes : 0;
     if (tab_bytes + slab_bytes > (size_t)SA_NOALLOC_SCRATCH_BYTES)
         return fail(SA_ERR_UNSUPPORTED, "replica state does not fit on chip and " + std::to_string(R) +
                                             " replicas exceed the fixed scratch of sa_run_noalloc (" +
                                             std::to_string(SA_NOALLOC_SCRATCH_BYTES) + " bytes)");
-    const int blocks = (R + rpc - 1) / rpc;
-    const size_t shared = in_global ? 0 : (size_t)rpc * rep_bytes;
 
     float* d_tab = reinterpret_cast<float*>(scratch);
     cudaError_t e = cudaMemcpyAsync(d_tab, tab.data(), 2 * (size_t)S * sizeof(float), cudaMemcpyHostToDevice, st);
@@ -187,18 +138,9 @@ extern "C" sa_status sa_run_noalloc(const sa_model* M, const sa_run_params* p, i
     a.energy_trace = p->energy_trace;
     a.drift_bits = nullptr;
     a.gstate = in_global ? scratch + tab_bytes : nullptr;   // every slab byte is written before it is read
-    a.rep_bytes = (int64_t)rep_bytes;
-    a.off_z = (int32_t)off_z;
-    a.off_cache = (int32_t)off_cache;
-    a.off_ctl = (int32_t)off_ctl;
-    a.off_list = (int32_t)off_list;
-    a.off_red = (int32_t)off_red;
-    a.off_lvl = lvl_on_chip ? (int32_t)off_lvl : -1;
-    a.rpc = rpc;
-    a.tpr = tpr;
-    a.heavy_links = heavy_links;
-    a.list_cap = list_cap;
-    const int le = sa::launch_sweep(a, mv.zbytes, p->rule, !in_global, blocks, rpc * tpr, shared, stream);
+    sa::plan_apply(plan, a);
+    const int le = sa::launch_sweep(a, mv.zbytes, p->rule, !in_global, plan.blocks, plan.rpc * plan.tpr,
+                                   (size_t)plan.shared_bytes, stream);
     if (le != 0) return fail(SA_ERR_CUDA, std::string("sweep launch: ") + cudaGetErrorString((cudaError_t)le));
     return SA_OK;
 }

@@ -3,6 +3,7 @@
 // server.cu) and the CUDA kernels.
 #pragma once
 
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 
@@ -161,6 +162,152 @@ inline int grow_threads_per_replica(int tpr, int32_t max_link_len, int heavy_lin
     int grown = (512 / per_block) / 32 * 32;
     if (grown > 256) grown = 256;
     return grown > tpr ? grown : tpr;
+}
+
+// ------------------------------------------------------------------ run planning
+// Host-side planning shared by every entry point that launches the sweep
+// kernel (sa_run, sa_run_noalloc, batches).  Pure arithmetic: no CUDA calls,
+// so that the same rules can be checked on a machine without a GPU.
+
+// What the planner needs to know about a compiled model.
+struct PlanModel {
+    int32_t n;
+    int32_t n_levels;
+    int32_t kind;               // KIND_QUIO / KIND_HUIO
+    int32_t is_float;
+    int32_t zbytes;             // bytes of one state offset z_k - l_k
+    int32_t max_link_len;
+    int64_t cache_elems;        // QUIO: n fields; HUIO: coefficient slots
+};
+
+inline PlanModel plan_model(const ModelView& v) {
+    return PlanModel{v.n, v.n_levels, v.dm.kind, v.is_float, v.zbytes, v.max_link_len, v.cache_elems};
+}
+
+// Per-replica state layout and launch shape of one run.
+struct RunPlan {
+    int32_t tpr;                // threads per replica (whole warps)
+    int32_t rpc;                // replicas per block
+    int32_t blocks;
+    int32_t heavy_links;        // update lists above this length go to the cooperative list
+    int32_t list_cap;           // entries of the cooperative list (6 ints each)
+    int32_t in_global;          // replica state in global memory instead of shared memory
+    int64_t rep_bytes;          // bytes of one replica's state region
+    int64_t shared_bytes;       // dynamic shared memory of one block
+    int32_t off_z, off_cache, off_ctl, off_list, off_red, off_lvl;
+};
+
+inline int64_t plan_round16(int64_t x) { return (x + 15) / 16 * 16; }
+
+// State layout of one replica for `tpr` threads: offsets z_k - l_k (zbytes
+// each), the cache (int64 or fp32), three list counters plus the flattened
+// length, the cooperative update list, the reduction scratch (one 8-byte word
+// per warp) and, when it takes at most 16 KB, the level boundary table.
+// `zbytes` may exceed the model's own (a batch uses its widest).  QUIO rows are
+// cheap per entry (one atomic) and go inline up to 64 links; HUIO incidences
+// cost a term product each and go inline up to 8.
+inline int64_t plan_layout(const PlanModel& m, int zbytes, int tpr, RunPlan* p) {
+    const bool huio = m.kind == KIND_HUIO;
+    const int64_t fsize = m.is_float ? 4 : 8;
+    p->tpr = tpr;
+    p->heavy_links = huio ? 8 : 64;
+    p->list_cap = huio ? 256 : 64;
+    p->off_z = 0;
+    p->off_cache = (int32_t)plan_round16((int64_t)m.n * zbytes);
+    p->off_ctl = (int32_t)plan_round16(p->off_cache + m.cache_elems * fsize);
+    p->off_list = p->off_ctl + 16;
+    p->off_red = (int32_t)plan_round16(p->off_list + (int64_t)p->list_cap * 24);
+    const int64_t lvl_bytes = (int64_t)(m.n_levels + 1) * 4;
+    const int64_t off_lvl = plan_round16(p->off_red + (int64_t)(tpr / 32) * 8);
+    const bool lvl_on_chip = lvl_bytes <= 16384;
+    p->off_lvl = lvl_on_chip ? (int32_t)off_lvl : -1;
+    p->rep_bytes = plan_round16(off_lvl + (lvl_on_chip ? lvl_bytes : 0));
+    return p->rep_bytes;
+}
+
+// Launch shape of a single-model run of R replicas.  tpr_req / rpc_req <= 0
+// leave the choice to the library: tpr from the mean level width (half of it,
+// rounded up to whole warps, 32..256), grown by grow_threads_per_replica for
+// long update lists; rpc as many replicas as shared memory and 512 threads
+// allow, but no more than needed to spread the replicas over the SMs.  Returns
+// nullptr, or a message describing the invalid request.
+inline const char* plan_run_shape(const PlanModel& m, int32_t R, int32_t tpr_req, int32_t rpc_req, bool force_global,
+                                  int sms, int64_t smem_max, RunPlan* p) {
+    int tpr = tpr_req;
+    if (tpr <= 0) {
+        const double mean_w = (double)m.n / (double)(m.n_levels > 0 ? m.n_levels : 1);
+        int want = (int)(mean_w / 2.0);
+        if ((double)want < mean_w / 2.0) ++want;
+        tpr = (want + 31) / 32 * 32;
+        tpr = tpr < 32 ? 32 : (tpr > 256 ? 256 : tpr);
+    }
+    if (tpr % 32 != 0 || tpr > 512 || tpr < 32) return "threads_per_replica must be a multiple of 32, <= 512";
+    if (tpr_req <= 0)
+        tpr = grow_threads_per_replica(tpr, m.max_link_len, m.kind == KIND_HUIO ? 8 : 64, R, rpc_req, sms);
+    const int64_t rep = plan_layout(m, m.zbytes, tpr, p);
+    int fit = (int)(smem_max / rep);
+    const int cap = 15 < 512 / tpr ? 15 : 512 / tpr;
+    fit = fit < cap ? fit : cap;
+    const bool in_global = fit < 1 || force_global;
+    int rpc = rpc_req;
+    if (rpc <= 0) {
+        int target = (R + (sms > 0 ? sms : 1) - 1) / (sms > 0 ? sms : 1);
+        target = target < 1 ? 1 : target;
+        rpc = in_global ? (target < cap ? target : cap) : (fit < target ? fit : target);
+    }
+    if (rpc < 1 || rpc > 15 || rpc * tpr > 512) return "replicas_per_block out of range";
+    if (!in_global && rpc > fit) return "replicas_per_block exceeds shared memory";
+    p->rpc = rpc;
+    p->in_global = in_global ? 1 : 0;
+    p->blocks = (R + rpc - 1) / rpc;
+    p->shared_bytes = in_global ? 0 : (int64_t)rpc * rep;
+    return nullptr;
+}
+
+// Per-sweep table read by the kernel: tab[s] = fp32(1 / T_s) with the geometric
+// schedule T_s = T_max (T_min / T_max)^(s / (S - 1)) of Sect. 3.1 (T_0 = T_max
+// when S = 1) or the caller's temperatures, and tab[S + s] = the OTM ratio
+// r_s = fp32(s) / fp32(S - 1) of Sect. 3.3.3 (0 when S = 1).  t_max and t_min
+// both <= 0 select the Sect. 3.4 temperatures -dE_max / ln(1/2) and
+// -dE_min / ln(0.001).  Returns nullptr or an error message.
+inline const char* plan_schedule(double de_max, double de_min, int32_t S, double t_max, double t_min,
+                                 const double* temps, float* tab) {
+    if (!temps) {
+        if (t_max <= 0 && t_min <= 0) {
+            t_max = -de_max / std::log(0.5);
+            t_min = -de_min / std::log(0.001);
+        } else if (!(t_max > 0 && t_min > 0) || !std::isfinite(t_max) || !std::isfinite(t_min)) {
+            return "t_max and t_min must both be positive (or both <= 0 for defaults)";
+        }
+    }
+    for (int32_t s = 0; s < S; ++s) {
+        double T;
+        if (temps) {
+            T = temps[s];
+            if (!(T > 0) || !std::isfinite(T)) return "temperatures must be positive";
+        } else {
+            const double frac = S > 1 ? (double)s / (double)(S - 1) : 0.0;
+            T = t_max * std::pow(t_min / t_max, frac);
+        }
+        tab[s] = (float)(1.0 / T);
+        tab[S + s] = S > 1 ? (float)s / (float)(S - 1) : 0.0f;
+    }
+    return nullptr;
+}
+
+// Copies the layout and shape of a plan into the kernel arguments.
+inline void plan_apply(const RunPlan& p, SweepArgs& a) {
+    a.rep_bytes = p.rep_bytes;
+    a.off_z = p.off_z;
+    a.off_cache = p.off_cache;
+    a.off_ctl = p.off_ctl;
+    a.off_list = p.off_list;
+    a.off_red = p.off_red;
+    a.off_lvl = p.off_lvl;
+    a.rpc = p.rpc;
+    a.tpr = p.tpr;
+    a.heavy_links = p.heavy_links;
+    a.list_cap = p.list_cap;
 }
 
 // Host-side launchers implemented in the .cu files.

@@ -900,8 +900,10 @@ __device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot,
     const int tpr = a.tpr;
     Z* zs = reinterpret_cast<Z*>(base + a.off_z);
     F* cache = reinterpret_cast<F*>(base + a.off_cache);
-    int* ctl = reinterpret_cast<int*>(base + a.off_ctl);      // [3] list counters
-    int* list = reinterpret_cast<int*>(base + a.off_list);    // [cap][3]: var, z_old, z_new
+    int* ctl = reinterpret_cast<int*>(base + a.off_ctl);      // [3] list counters, [3] flattened length
+    // [cap][6]: variable k, z_old, z_new, link_begin, link_len, prefix of the
+    // flattened (entry, link) pairs
+    int* list = reinterpret_cast<int*>(base + a.off_list);
     Acc* red = reinterpret_cast<Acc*>(base + a.off_red);
 
     // ---- random initial state (Sect. 3.1), or the caller's

@@ -40,3 +40,68 @@ def test_grow_threads_per_replica(tmp_path):
     for c, g in zip(CASES, got):
         per_block = c[4] if c[4] > 0 else max(1, min(15, -(-c[3] // c[5])))
         assert g % 32 == 0 and g <= 256 and (g == c[0] or per_block * g <= 512)
+
+
+def _compile_and_run(tmp_path, body):
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not available")
+    src = tmp_path / "plan.cpp"
+    src.write_text('#include "sa_internal.h"\n#include <cstdio>\nint main() {\n' + body + "\n  return 0; }\n")
+    exe = tmp_path / "plan"
+    subprocess.run([gxx, "-std=c++17", "-O1", "-I", os.path.join(ROOT, "paper_2511_17245_gb300", "csrc"),
+                    str(src), "-o", str(exe)], check=True)
+    return subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+
+
+def test_plan_run_shape_benchmark_workload(tmp_path):
+    """The 10,000-variable [0,255] fp32 workload (43 levels) with 1024 replicas on
+    152 SMs and 227 KB of shared memory per block: 128 threads per replica,
+    51,760 bytes of state each, 4 replicas per block, 256 blocks."""
+    body = """
+  sa::PlanModel m{10000, 43, sa::KIND_QUIO, 1, 1, 40, 10000};
+  sa::RunPlan p{};
+  const char* err = sa::plan_run_shape(m, 1024, 0, 0, false, 152, 232448, &p);
+  std::printf("%d %d %d %d %lld %lld %d %d %d %d %d %d\\n", err == nullptr, p.tpr, p.rpc, p.blocks,
+              (long long)p.rep_bytes, (long long)p.shared_bytes, p.in_global, p.off_cache, p.off_ctl,
+              p.off_list, p.off_red, p.off_lvl);
+  err = sa::plan_run_shape(m, 1024, 0, 0, true, 152, 232448, &p);
+  std::printf("%d %d %d %lld\\n", err == nullptr, p.in_global, p.rpc, (long long)p.shared_bytes);
+  err = sa::plan_run_shape(m, 1024, 48, 0, false, 152, 232448, &p);
+  std::printf("%d\\n", err == nullptr);
+  err = sa::plan_run_shape(m, 1024, 128, 5, false, 152, 232448, &p);
+  std::printf("%d\\n", err == nullptr);
+"""
+    out = _compile_and_run(tmp_path, body)
+    assert out[:12] == ["1", "128", "4", "256", "51760", "207040", "0", "10000", "50000", "50016", "51552", "51584"]
+    assert out[12:16] == ["1", "1", "4", "0"]          # forced global state: same shape, no shared memory
+    assert out[16] == "0"                               # 48 threads: not whole warps
+    assert out[17] == "0"                               # 5 replicas of 51,760 bytes exceed shared memory
+
+
+def test_plan_schedule_closed_form(tmp_path):
+    """Geometric schedule of Sect. 3.1 as fp32 inverse temperatures, OTM ratio
+    s/(S-1), the single-sweep case, the Sect. 3.4 defaults and rejections."""
+    body = """
+  float tab[10];
+  const char* err = sa::plan_schedule(0, 0, 5, 100.0, 0.01, nullptr, tab);
+  for (int i = 0; i < 10; ++i) std::printf("%.9g\\n", tab[i]);
+  std::printf("%d\\n", err == nullptr);
+  err = sa::plan_schedule(0, 0, 1, 7.0, 0.5, nullptr, tab);
+  std::printf("%.9g %.9g %d\\n", tab[0], tab[1], err == nullptr);
+  err = sa::plan_schedule(3.0, 2.0, 2, 0.0, 0.0, nullptr, tab);
+  std::printf("%.9g %.9g %d\\n", tab[0], tab[1], err == nullptr);
+  double temps[2] = {4.0, -1.0};
+  std::printf("%d %d\\n", sa::plan_schedule(0, 0, 2, 0, 0, temps, tab) != nullptr,
+              sa::plan_schedule(0, 0, 2, 5.0, 0.0, nullptr, tab) != nullptr);
+"""
+    out = [float(x) for x in _compile_and_run(tmp_path, body)]
+    import numpy as np
+    T = 100.0 * (0.01 / 100.0) ** (np.arange(5) / 4)
+    np.testing.assert_array_equal(np.array(out[:5], np.float32), (1.0 / T).astype(np.float32))
+    np.testing.assert_array_equal(np.array(out[5:10], np.float32), np.float32([0, 0.25, 0.5, 0.75, 1.0]))
+    assert out[10] == 1
+    assert out[11:14] == [np.float32(1 / 7.0), 0.0, 1]
+    tmax, tmin = -3.0 / np.log(0.5), -2.0 / np.log(0.001)
+    assert out[14] == np.float32(1 / tmax) and out[15] == np.float32(1 / tmin) and out[16] == 1
+    assert out[17:19] == [1, 1]

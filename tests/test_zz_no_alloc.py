@@ -56,12 +56,22 @@ def test_noalloc_equals_sa_run_twice(rule):
 
 def test_noalloc_state_in_scratch_slab():
     """Replica state kept in the fixed scratch (global placement) instead of
-    shared memory: same results as sa_run, twice."""
+    shared memory: same results as sa_run on two calls, with a run of another
+    model in between (other replica count, other state size and layout) that
+    leaves its own data in the array, so that a byte read before it is written
+    would show."""
     m = Model(wl.huio_zipf(6, n=300, n_quad=600, n_cubic=900, n_quartic=200, lo=-9, hi=9))
-    kw = dict(t_max=300.0, t_min=1.0, flags=_lib.SA_FLAG_STATE_IN_GLOBAL)
+    other = Model(wl.quio_sparse_int(9, n=517, n_edges=2100, lo=-70, hi=900, jmax=5, hmax=40, dmax=3))
+    glob = _lib.SA_FLAG_STATE_IN_GLOBAL
+    kw = dict(t_max=300.0, t_min=1.0, flags=glob)
     ref = m.run("metropolis", 40, 12, seed=3, **kw)
-    for _ in range(2):
-        assert _same(_noalloc(m, "metropolis", 40, 12, 3, **kw), ref)
+    ref_other = other.run("heat_bath", 25, 29, seed=5, t_max=80.0, t_min=0.5, flags=glob)
+    first = _noalloc(m, "metropolis", 40, 12, 3, **kw)
+    mid = _noalloc(other, "heat_bath", 25, 29, 5, t_max=80.0, t_min=0.5, flags=glob)
+    second = _noalloc(m, "metropolis", 40, 12, 3, **kw)
+    assert _same(first, ref)
+    assert _same(mid, ref_other)
+    assert _same(second, ref)
 
 
 def test_noalloc_float_model_within_tolerance():
