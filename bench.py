@@ -37,18 +37,49 @@ WORKLOAD = "quio_sparse_wide"
 METRIC = "variable-update attempts/s"
 UNIT = "attempts/s"
 L2_FLUSH_BYTES = 512 << 20
-# DRAM bytes (read + write) of one heat-bath launch from an ncu capture of this
-# kernel (profiles/sweep_heat_bath_quio_sparse_wide.md); the model and the
-# replica state stay in L2 / shared memory, so it does not grow with sweeps.
-HB_TRAFFIC_BYTES = 2.757e6
+MEAN_DEGREE = 2 * N_EDGES / N_VARS
 
 
 def _peaks():
+    """Measured HBM copy bandwidth and bf16 rate of this machine's GPUs."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return json.load(f), "measured"
     except Exception:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def rule_roofline(rule, ms, attempts, change_rate, width, peaks_dev):
+    """Roofline of one rule's sweep launch on the benchmark workload, from the
+    algorithmic work per attempt (one attempt = one variable visit of one
+    replica) and the ceilings measured on this GPU by sa_measure_peaks:
+      heat bath   u - l + 1 weights, one exp2 each (Eq. prob_heatbath), against
+                  the SFU exp2 rate;
+      Metropolis, OTM  replica state in shared memory: read z_k (1 B) and f_k
+                  (4 B), and per change write z_k (1 B) and read-modify-write the
+                  deg neighbour fields (8 B each), against the shared-memory
+                  bandwidth; the changed variable's CSR row (deg x (4 B column +
+                  4 B value)) from L2, against the L2-resident copy bandwidth.
+    `change_rate` is this rule's measured fraction of attempts that changed
+    the variable."""
+    sec = ms / 1e3
+    deg = MEAN_DEGREE
+    if rule == "heat_bath":
+        work = attempts * width
+        ach = work / sec
+        return {"bound": "alu", "unit": "exp2/s", "achieved": ach, "peak": peaks_dev["exp2_per_s"],
+                "frac": ach / peaks_dev["exp2_per_s"], "work_per_attempt": f"{width} exp2",
+                "peak_source": "sa_measure_peaks exp2 (SFU), measured in this run"}
+    smem_b = 5 + change_rate * (1 + 8 * deg)
+    l2_b = change_rate * 8 * deg
+    smem_gbs = attempts * smem_b / sec / 1e9
+    l2_gbs = attempts * l2_b / sec / 1e9
+    return {"bound": "smem", "unit": "GB/s", "achieved": smem_gbs, "peak": peaks_dev["smem_gbs"],
+            "frac": smem_gbs / peaks_dev["smem_gbs"], "bytes_per_attempt": smem_b,
+            "l2": {"achieved": l2_gbs, "peak": peaks_dev["l2_gbs"], "frac": l2_gbs / peaks_dev["l2_gbs"],
+                   "bytes_per_attempt": l2_b},
+            "change_rate": change_rate,
+            "peak_source": "sa_measure_peaks shared-memory and L2-resident copy, measured in this run"}
 
 
 def _config(extra=None):
@@ -383,11 +414,14 @@ def main():
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    from paper_2511_17245_gb300 import Model, make_params, sa_model_create, sa_model_destroy, sa_run
+    from paper_2511_17245_gb300 import (Model, make_params, sa_measure_peaks, sa_model_create, sa_model_destroy,
+                                        sa_run, sa_run_report)
     from paper_2511_17245_gb300 import build as pkg_build
     from paper_2511_17245_gb300 import workloads as wl
     pkg_build.build()
     rules = args.rules.split(",")
+    # ceilings of this GPU (SFU exp2, FMA, L2-resident copy, shared memory)
+    peaks_dev = sa_measure_peaks(torch.cuda.current_stream().cuda_stream)
 
     inst = wl.quio_sparse_wide(1, n=N_VARS, n_edges=N_EDGES, lo=LO, hi=HI)
     model = Model(inst)
@@ -413,7 +447,22 @@ def main():
                 e1.record(stream)
                 record.append((rule, e0, e1))
 
-    for _ in range(args.warmup):
+    # first warm-up step: each rule once with a report (launch shape, refresh
+    # drift) and its change rate; the rest plain
+    change_rates, reports = {}, {}
+    for rule in rules:
+        rep = sa_run_report()
+        p = make_params(rule, S, R, seed=rank, t_max=tmax, t_min=tmin, refresh_interval=REFRESH, report=rep)
+        sa_run(model.handle, p, states, energies, accepts, sptr)
+        torch.cuda.synchronize()
+        change_rates[rule] = float(accepts.double().mean().item()) / (n * S)
+        e_re = model.energy(states).double()
+        rel = ((energies - e_re).abs() / e_re.abs().clamp_min(1e-300)).max().item()
+        reports[rule] = {"threads_per_replica": rep.threads_per_replica, "replicas_per_block": rep.replicas_per_block,
+                         "blocks": rep.blocks, "shared_bytes": rep.shared_bytes,
+                         "max_refresh_drift": rep.max_refresh_drift,
+                         "final_energy_max_rel_err_vs_fp64_recompute": rel}
+    for _ in range(max(0, args.warmup - 1)):
         one_step()
     torch.cuda.synchronize()
 
@@ -449,37 +498,20 @@ def main():
     for rule in rules:
         ms = [a.elapsed_time(b) for (rr, a, b) in recs if rr == rule]
         per_rule[rule] = {"ms": float(np.mean(ms)), "attempts_per_s": attempts_per_run / (np.mean(ms) / 1000)}
-    acc_rate = float(accepts.double().mean().item()) / (n * S)
-
-    # ---- roofline of the dominant kernel (longest rule launch)
+    # ---- rooflines: every rule against its own ceiling, the dominant (longest)
+    # launch as the headline; ceilings measured on this GPU in this run
     peaks, peak_kind = _peaks()
     dom = max(per_rule, key=lambda r: per_rule[r]["ms"])
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    roof = None
-    if dom == "heat_bath":
-        # algorithmic: one exp per candidate value (u - l + 1 = 256) per attempt;
-        # peak: SFU exp2 at 16 results / clock / SM x 152 SMs x max SM clock
-        work = attempts_per_run * (HI - LO + 1)
-        achieved = work / (per_rule[dom]["ms"] / 1000.0) / 1e12
-        peak = 16 * 152 * sm_max * 1e6 / 1e12
-        roof = {"bound": "alu", "kernel": f"sweep_kernel<{dom}>", "achieved": achieved, "peak": peak,
-                "unit": "Texp/s", "frac": achieved / peak, "traffic": HB_TRAFFIC_BYTES,
-                "peak_source": f"SFU 16/clk/SM x 152 SMs x {sm_max:.0f} MHz ({peak_kind} clock)",
-                "note": "algorithmic work = u-l+1 exp2 per attempt (Eq. prob_heatbath); the kernel evaluates only "
-                        "the window that carries all but e^-20 of the weight, so this is effective throughput; "
-                        "traffic = DRAM bytes per launch from ncu (profiles/sweep_heat_bath_quio_sparse_wide.md)"}
-    else:
-        # algorithmic bytes per attempt: read z_k (1 B) + f_k (4 B); on a change
-        # write z_k (1 B) and read-modify-write deg fields (8 B each) plus the
-        # CSR row (8 B per entry) shared by the replicas of a block
-        deg = 2 * N_EDGES / N_VARS
-        bpa = 5 + acc_rate * (1 + 8 * deg)
-        achieved = attempts_per_run * bpa / (per_rule[dom]["ms"] / 1000.0) / 1e9
-        peak = float(peaks["hbm_gbs"])
-        roof = {"bound": "hbm", "kernel": f"sweep_kernel<{dom}>", "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": f"hbm_gbs ({peak_kind})"}
-
+    per_rule_roof = {}
+    for rule in rules:
+        per_rule_roof[rule] = rule_roofline(rule, per_rule[rule]["ms"], attempts_per_run, change_rates[rule],
+                                            HI - LO + 1, peaks_dev)
+        per_rule[rule]["change_rate"] = change_rates[rule]
+    roof = dict(per_rule_roof[dom])
+    roof["kernel"] = f"sweep_kernel<{dom}>"
+    roof["traffic"] = None
+    roof["limiter"] = ("ncu: latency-bound (few warps per SM: the replica state fills shared memory; "
+                       "per-level barriers; dependent decision chains), not the listed ceiling")
     # ---- e2e through the C ABI with host buffers (model upload + host outputs each step)
     e2e = None
     if rank == 0 and not args.no_e2e:
@@ -528,8 +560,11 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 refresh)", "data": "synthetic",
                 "config": _config({"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                                    "replicas": R, "sweeps": S}),
-                "per_rule": per_rule, "accept_rate_last_rule": acc_rate,
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "per_rule": per_rule, "roofline": roof, "roofline_per_rule": per_rule_roof,
+                "peaks_measured": {k: peaks_dev[k] for k in ("exp2_per_s", "fma_per_s", "l2_gbs", "smem_gbs",
+                                                            "smem_atomic_per_s", "sms")},
+                "peaks_driver": {"hbm_gbs": peaks.get("hbm_gbs"), "source": peak_kind},
+                "run_reports": reports, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": len(rules) * args.steps, "clocks": clocks}
         if small is not None:
             line["small_configs"] = small

@@ -10,14 +10,14 @@ from __future__ import annotations
 from . import _lib
 from ._lib import (RULES, SAError, make_params, sa_batch_autotune, sa_batch_create, sa_batch_destroy,
                    sa_batch_get_info, sa_batch_result, sa_batch_run, sa_default_temperatures, sa_energy,
-                   sa_last_error, sa_model_create, sa_model_create_quio_dense, sa_model_destroy, sa_model_get_info,
-                   sa_run, sa_run_noalloc, sa_run_report, sa_server_cancel, sa_server_create, sa_server_destroy,
-                   sa_server_get_stats, sa_server_poll, sa_server_result, sa_server_submit, sa_server_wait,
-                   sa_version)
+                   sa_last_error, sa_measure_peaks, sa_model_create, sa_model_create_quio_dense,
+                   sa_model_destroy, sa_model_get_info, sa_run, sa_run_noalloc, sa_run_report, sa_server_cancel,
+                   sa_server_create, sa_server_destroy, sa_server_get_stats, sa_server_poll, sa_server_result,
+                   sa_server_submit, sa_server_wait, sa_version)
 
 __all__ = ["Model", "RULES", "SAError", "make_params", "sa_batch_autotune", "sa_batch_create", "sa_batch_destroy",
            "sa_batch_get_info", "sa_batch_result", "sa_batch_run", "sa_default_temperatures", "sa_energy",
-           "sa_last_error", "sa_model_create", "sa_model_create_quio_dense", "sa_model_destroy",
+           "sa_last_error", "sa_measure_peaks", "sa_model_create", "sa_model_create_quio_dense", "sa_model_destroy",
            "sa_model_get_info", "sa_run", "sa_run_noalloc", "sa_run_report", "sa_server_cancel", "sa_server_create",
            "sa_server_destroy", "sa_server_get_stats", "sa_server_poll", "sa_server_result", "sa_server_submit",
            "sa_server_wait", "sa_version"]

@@ -63,6 +63,13 @@ class sa_server_stats(C.Structure):
                 ("attempts_per_s", C.c_double)]
 
 
+class sa_peaks(C.Structure):
+    _fields_ = [("exp2_per_s", C.c_double), ("fma_per_s", C.c_double), ("l2_gbs", C.c_double),
+                ("smem_gbs", C.c_double), ("smem_atomic_per_s", C.c_double), ("sms", C.c_int32),
+                ("l2_buffer_bytes", C.c_int32), ("exp2_ms", C.c_float), ("fma_ms", C.c_float),
+                ("l2_ms", C.c_float), ("smem_ms", C.c_float), ("smem_atomic_ms", C.c_float)]
+
+
 class sa_run_params(C.Structure):
     _fields_ = [("rule", C.c_int32), ("n_sweeps", C.c_int32), ("n_replicas", C.c_int32),
                 ("refresh_interval", C.c_int32), ("seed", C.c_uint64), ("t_max", C.c_double),
@@ -73,12 +80,13 @@ class sa_run_params(C.Structure):
                 ("report", C.POINTER(sa_run_report))]
 
 
-# Every symbol include/sa.h declares (checked by the tests).
+# Every symbol include/*.h declares (checked by the tests).
 EXPORTS = ["sa_model_create", "sa_model_destroy", "sa_model_get_info", "sa_default_temperatures",
            "sa_run", "sa_energy", "sa_last_error", "sa_version", "sa_run_noalloc", "sa_model_create_quio_dense",
            "sa_batch_create", "sa_batch_autotune", "sa_batch_run", "sa_batch_result", "sa_batch_get_info",
            "sa_batch_destroy", "sa_server_create", "sa_server_submit", "sa_server_poll", "sa_server_wait",
-           "sa_server_cancel", "sa_server_result", "sa_server_get_stats", "sa_server_destroy"]
+           "sa_server_cancel", "sa_server_result", "sa_server_get_stats", "sa_server_destroy",
+           "sa_measure_peaks"]
 SA_REQ_QUEUED, SA_REQ_RUNNING, SA_REQ_DONE, SA_REQ_FAILED, SA_REQ_CANCELLED = range(5)
 # size of the fixed device scratch array behind sa_run_noalloc (SA_NOALLOC_SCRATCH_BYTES)
 NOALLOC_SCRATCH_BYTES = 4 << 20
@@ -137,6 +145,8 @@ def load():
         lib.sa_server_get_stats.restype = C.c_int
         lib.sa_server_destroy.argtypes = [P]
         lib.sa_server_destroy.restype = None
+        lib.sa_measure_peaks.argtypes = [C.POINTER(sa_peaks), P]
+        lib.sa_measure_peaks.restype = C.c_int
         lib.sa_energy.argtypes = [P, P, C.c_int64, P, P]
         lib.sa_energy.restype = C.c_int
         lib.sa_last_error.argtypes = []
@@ -239,6 +249,14 @@ def sa_run_noalloc(h, params: sa_run_params, out_states, out_energies, out_accep
     """sa_run for callers that cannot allocate: device buffers only; the run's
     scratch is the library's fixed device array (see include/sa.h)."""
     _check(load().sa_run_noalloc(h, C.byref(params), ptr(out_states), ptr(out_energies), ptr(out_accepts), stream))
+
+
+def sa_measure_peaks(stream=None) -> dict:
+    """Measured SFU exp2, FMA, L2-copy and shared-memory ceilings of the current
+    device (include/sa_peaks.h)."""
+    pk = sa_peaks()
+    _check(load().sa_measure_peaks(C.byref(pk), stream))
+    return {f: getattr(pk, f) for f, _ in pk._fields_}
 
 
 def sa_energy(h, states, n_states, energies, stream=None):

@@ -36,7 +36,7 @@ def sources():
 
 def _deps_mtime():
     ts = [os.path.getmtime(os.path.join(CSRC, f)) for f in os.listdir(CSRC)]
-    ts.append(os.path.getmtime(os.path.join(INCLUDE, "sa.h")))
+    ts += [os.path.getmtime(os.path.join(INCLUDE, f)) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     ts.append(os.path.getmtime(__file__))
     return max(ts)
 

@@ -253,6 +253,7 @@ sa_status compile_terms(sa_model* M, int32_t n, const int64_t* lower, const int6
     DevModel& dm = M->dm;
     dm.n = n;
     dm.is_float = M->is_float ? 1 : 0;
+    dm.max_width = M->max_width;
     dm.const_i = (int64_t)const_i;
     dm.const_d = const_d;
     struct Offs {

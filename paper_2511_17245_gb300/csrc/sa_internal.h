@@ -40,6 +40,8 @@ struct DevModel {
     int32_t kind;
     int32_t is_float;
     int32_t n_levels;
+    uint32_t max_width;         // largest u_k - l_k
+    int32_t _pad0;
     const VarMeta* meta;        // [n]
     const int32_t* lvl_ptr;     // [n_levels + 1]
     const int32_t* lvl_vars;    // [n]: variables grouped by dependency level
@@ -262,6 +264,69 @@ inline const char* plan_run_shape(const PlanModel& m, int32_t R, int32_t tpr_req
     p->blocks = (R + rpc - 1) / rpc;
     p->shared_bytes = in_global ? 0 : (int64_t)rpc * rep;
     return nullptr;
+}
+
+// ------------------------------------------------------------------ time-sliced runs
+// When R replicas exceed the P thread groups that can be resident at once, a
+// plain launch runs ceil(R / P) waves and the last one leaves slots idle.  A
+// time-sliced launch instead gives every slot p an equal share of the
+// flattened sequence u = r S + s of (replica, sweep) pairs: a contiguous range
+// of Q_p = floor(R S / P) or one more pairs, Q_p >= S when R >= P.  A replica
+// cut by a range boundary has its first sweeps (the head) at the end of slot
+// p's range and its last sweeps (the tail) at the start of slot p + 1's range;
+// each slot runs its head piece first, then its whole replicas, then its tail
+// piece.  The head on slot p ends after s_b sweeps of that slot and the tail on
+// slot p + 1 starts after Q_{p+1} - (S - s_b) >= s_b sweeps of its slot, so the
+// handoff of the replica's state never waits on work queued behind it.
+struct SlicePiece {
+    int32_t r;          // replica
+    int32_t s0, s1;     // sweeps [s0, s1)
+};
+struct SlicePlan {
+    int32_t n;          // pieces (0..3 groups: head, whole replicas as a range, tail)
+    SlicePiece head;    // s0 == 0, s1 < S (valid if has_head)
+    int32_t has_head;
+    int32_t whole_r0, whole_r1;   // whole replicas [whole_r0, whole_r1)
+    SlicePiece tail;    // s0 > 0, s1 == S (valid if has_tail)
+    int32_t has_tail;
+};
+
+// Pieces of slot p (0 <= p < P) for R replicas of S sweeps over P slots.
+inline
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+SlicePlan slice_plan(int64_t p, int32_t R, int32_t S, int64_t P) {
+    SlicePlan sp{};
+    sp.whole_r0 = sp.whole_r1 = 0;
+    const int64_t total = (int64_t)R * S;
+    const int64_t base = total / P, rem = total % P;
+    const int64_t u0 = p * base + (p < rem ? p : rem);
+    const int64_t u1 = u0 + base + (p < rem ? 1 : 0);
+    if (u0 >= u1) return sp;
+    int32_t r_first = (int32_t)(u0 / S), s_first = (int32_t)(u0 % S);
+    const int32_t r_last = (int32_t)((u1 - 1) / S), s_end = (int32_t)((u1 - 1) % S) + 1;
+    if (s_first > 0) {
+        // the range starts inside replica r_first: its tail (its head is on slot p - 1)
+        sp.has_tail = 1;
+        sp.tail = SlicePiece{r_first, s_first, r_first == r_last ? s_end : S};
+        ++r_first;
+        s_first = 0;
+    }
+    if (r_first <= r_last) {
+        if (s_end < S) {
+            // the range ends inside replica r_last: its head (its tail is on slot p + 1)
+            sp.has_head = 1;
+            sp.head = SlicePiece{r_last, 0, s_end};
+            sp.whole_r0 = r_first;
+            sp.whole_r1 = r_last;
+        } else {
+            sp.whole_r0 = r_first;
+            sp.whole_r1 = r_last + 1;
+        }
+    }
+    sp.n = sp.has_head + sp.has_tail + (sp.whole_r1 - sp.whole_r0);
+    return sp;
 }
 
 // Per-sweep table read by the kernel: tab[s] = fp32(1 / T_s) with the geometric

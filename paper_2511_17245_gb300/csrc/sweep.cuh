@@ -328,13 +328,6 @@ __device__ __forceinline__ float ex2_ftz(float x) {
     return y;
 }
 
-// Explicit inverse CDF over all u-l+1 values (Eq. prob_heatbath).
-// Integer models: three passes over the candidates (minimum dE, compensated
-// total, compensated search) with fp32 weights expf(-fp32(dE_v - dE_min) beta),
-// the convention shared with the oracle.
-// Float models: the same three passes with the candidate value carried as an
-// exact float counter (no integer conversions in the loop) and weights
-// 2^((dE_min - dE_v) beta log2 e).
 // Weights below exp(-(20 + ln n)) times the largest one are left out of the
 // heat-bath sum: with n candidates their total is below e^-20 of the total,
 // far inside the near-threshold margin of the decision.  Candidates are
@@ -367,6 +360,44 @@ __device__ __forceinline__ F quio_interval_min(const VarView<F, KIND_QUIO>& vv, 
     return mnb;
 }
 
+// Kept window [wb0, wb1] of the blocks of 32 values of a QUIO variable
+// (blocks counted from lo; nblk = width / 32 + 1 on entry as wb1 + 1): for a
+// convex variable (J_kk > 0) the block lower bound of dE falls and then rises,
+// so the first and last kept blocks are found by bisection on either side of
+// the vertex; otherwise (or if rounding hides the vertex block) every block.
+template <class F>
+__device__ __forceinline__ void hb_quio_window(const VarView<F, KIND_QUIO>& vv, long long z, long long lo,
+                                               uint32_t width, F mn, float beta, uint32_t& wb0, uint32_t& wb1) {
+    constexpr uint32_t B = 32;
+    if (!(vv.d > F(0))) return;
+    const uint32_t nblk = wb1 + 1;
+    const float cutv = hb_cut(width);
+    auto kept = [&](uint32_t b) -> bool {
+        const long long v0 = lo + (long long)(b * B);
+        const long long v1 = lo + (long long)min(width, b * B + (B - 1));
+        return Num<F>::to_f(quio_interval_min<F>(vv, z, v0, v1) - mn) * beta <= cutv;
+    };
+    // block holding the minimum
+    long long vstar;
+    if constexpr (Num<F>::is_float) {
+        float qv = floorf(-(float)vv.f / (2.f * (float)vv.d));
+        qv = fminf(fmaxf(qv, (float)lo), (float)(lo + (long long)width));
+        vstar = (long long)qv;
+    } else {
+        vstar = floor_div(-vv.f, 2 * vv.d);
+        if (vstar < lo) vstar = lo;
+        if (vstar > lo + (long long)width) vstar = lo + (long long)width;
+    }
+    const uint32_t bm = (uint32_t)(vstar - lo) / B;
+    if (!kept(bm)) return;  // rounding: keep every block
+    uint32_t a = 0, c = bm;  // first kept block in [0, bm]
+    while (a < c) { const uint32_t mid = (a + c) / 2; if (kept(mid)) c = mid; else a = mid + 1; }
+    wb0 = a;
+    a = bm; c = nblk - 1;    // last kept block in [bm, nblk-1]
+    while (a < c) { const uint32_t mid = (a + c + 1) / 2; if (kept(mid)) a = mid; else c = mid - 1; }
+    wb1 = a;
+}
+
 // Explicit inverse CDF over all u-l+1 values (Eq. prob_heatbath).
 // Integer models: three passes over the candidates (minimum dE, compensated
 // total, compensated search) with fp32 weights expf(-fp32(dE_v - dE_min) beta),
@@ -392,42 +423,9 @@ __device__ long long heat_bath_general(const VarView<F, KIND>& vv, long long z, 
             mn = de < mn ? de : mn;
         }
     }
-    // kept window [wb0, wb1] of blocks: for a convex QUIO variable the block
-    // lower bound falls and then rises, so the first and last kept blocks are
-    // found by bisection on either side of the vertex; otherwise every block.
+    // kept window [wb0, wb1] of blocks
     uint32_t wb0 = 0, wb1 = nblk - 1;
-    if constexpr (KIND == KIND_QUIO) {
-        if (vv.d > F(0)) {
-            const float cutv = hb_cut(width);
-            auto kept = [&](uint32_t b) -> bool {
-                const long long v0 = lo + (long long)(b * B);
-                const long long v1 = lo + (long long)min(width, b * B + (B - 1));
-                return Num<F>::to_f(quio_interval_min<F>(vv, z, v0, v1) - mn) * beta <= cutv;
-            };
-            // block holding the minimum
-            long long vstar;
-            if constexpr (Num<F>::is_float) {
-                float qv = floorf(-(float)vv.f / (2.f * (float)vv.d));
-                qv = fminf(fmaxf(qv, (float)lo), (float)(lo + (long long)width));
-                vstar = (long long)qv;
-            } else {
-                vstar = floor_div(-vv.f, 2 * vv.d);
-                if (vstar < lo) vstar = lo;
-                if (vstar > lo + (long long)width) vstar = lo + (long long)width;
-            }
-            uint32_t bm = (uint32_t)(vstar - lo) / B;
-            if (!kept(bm)) {  // rounding: fall back to every block
-                bm = 0;
-            } else {
-                uint32_t a = 0, c = bm;  // first kept block in [0, bm]
-                while (a < c) { const uint32_t mid = (a + c) / 2; if (kept(mid)) c = mid; else a = mid + 1; }
-                wb0 = a;
-                a = bm; c = nblk - 1;   // last kept block in [bm, nblk-1]
-                while (a < c) { const uint32_t mid = (a + c + 1) / 2; if (kept(mid)) a = mid; else c = mid - 1; }
-                wb1 = a;
-            }
-        }
-    }
+    if constexpr (KIND == KIND_QUIO) hb_quio_window<F>(vv, z, lo, width, mn, beta, wb0, wb1);
     if constexpr (Num<F>::is_float) {
         const float zf = __int2float_rn((int)z), v0f = __int2float_rn((int)lo);
         const float b2 = beta * 1.4426950408889634f, mb = (float)mn * b2;
@@ -491,6 +489,128 @@ __device__ long long heat_bath_general(const VarView<F, KIND>& vv, long long z, 
         }
         return last;
     }
+}
+
+// ------------------------------------------------------------------ warp-parallel heat bath
+// A pair hi + lo added with Knuth's TwoSum: the rounding error of hi + hi' is
+// kept in lo, so that sums over many lanes stay within a few ulp.
+struct CompF {
+    float hi, lo;
+};
+__device__ __forceinline__ CompF comp_add(CompF a, CompF b) {
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b.hi - bb);
+    return {s, e + (a.lo + b.lo)};
+}
+
+template <class T>
+__device__ __forceinline__ T warp_min(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const T u = __shfl_xor_sync(0xffffffffu, v, o);
+        v = u < v ? u : v;
+    }
+    return v;
+}
+
+// The inverse CDF of Eq. prob_heatbath for one variable, evaluated by the 32
+// lanes of a warp together (all lanes call it with the same arguments and
+// receive the same value).  Same weights, candidate window and pick rule as
+// heat_bath_general (smallest v with C_v >= Uc C_total):
+//   1. dE_min: closed form for QUIO, lane-strided minimum for HUIO;
+//   2. the kept candidates [c0, c1] are cut into 32 contiguous segments, one
+//      per lane; each lane sums its weights (Kahan) and the warp forms the
+//      inclusive prefix of the segment sums with compensated pairs;
+//   3. the first lane whose inclusive prefix reaches Uc C_total walks its
+//      segment from its exclusive prefix and picks the value.
+// The lanes therefore touch each candidate once for the total and one
+// segment once more for the pick, instead of one lane walking all of them.
+template <class F, int KIND>
+__device__ long long heat_bath_warp(const VarView<F, KIND>& vv, long long z, long long lo, uint32_t width,
+                                    uint32_t xu, float beta, int lane) {
+    constexpr uint32_t B = 32;
+    constexpr unsigned full = 0xffffffffu;
+    F mn = F(0);
+    if constexpr (KIND == KIND_QUIO) {
+        const F e = quio_interval_min<F>(vv, z, lo, lo + (long long)width);
+        mn = e < mn ? e : mn;
+    } else {
+        for (uint32_t i = (uint32_t)lane; i <= width; i += 32) {
+            const F de = vv.delta(z, lo + (long long)i);
+            mn = de < mn ? de : mn;
+        }
+        mn = warp_min(mn);
+    }
+    uint32_t wb0 = 0, wb1 = width / B;
+    if constexpr (KIND == KIND_QUIO) hb_quio_window<F>(vv, z, lo, width, mn, beta, wb0, wb1);
+    const uint32_t c0 = wb0 * B, c1 = min(width, wb1 * B + (B - 1));
+    const uint32_t m = (c1 - c0) / 32 + 1;                 // segment length
+    const uint32_t s0 = c0 + (uint32_t)lane * m;           // this lane's segment [s0, s1]
+    const bool has = s0 <= c1;
+    const uint32_t s1 = has ? min(c1, s0 + (m - 1)) : 0u;
+    const float zf = __int2float_rn((int)z), v0f = __int2float_rn((int)lo);
+    const float b2 = beta * 1.4426950408889634f, mb = Num<F>::to_f(mn) * b2;
+    auto weight = [&](uint32_t i) -> float {
+        if constexpr (Num<F>::is_float) {
+            return ex2_ftz(fmaf(-vv.delta_ff(zf, v0f + (float)i), b2, mb));
+        } else {
+            return expf(-(Num<F>::to_f(vv.delta(z, lo + (long long)i) - mn) * beta));
+        }
+    };
+    float sum = 0.f, comp = 0.f;
+    if (has) {
+        for (uint32_t i = s0; i <= s1; ++i) {
+            const float y = weight(i) - comp;
+            const float t = sum + y;
+            comp = (t - sum) - y;
+            sum = t;
+        }
+    }
+    CompF v{sum, -comp};
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const CompF u{__shfl_up_sync(full, v.hi, o), __shfl_up_sync(full, v.lo, o)};
+        if (lane >= o) v = comp_add(u, v);
+    }
+    const float tot = __shfl_sync(full, v.hi, 31) + __shfl_sync(full, v.lo, 31);
+    const float thr = unit_open_left(xu) * tot;
+    CompF ex{__shfl_up_sync(full, v.hi, 1), __shfl_up_sync(full, v.lo, 1)};
+    if (lane == 0) ex = CompF{0.f, 0.f};
+    const unsigned hit = __ballot_sync(full, has && (v.hi + v.lo) >= thr);
+    const unsigned nonempty = __ballot_sync(full, has);
+    // rounding can leave the threshold above the last prefix: take the last segment
+    const int sel = hit ? __ffs(hit) - 1 : 31 - __clz(nonempty);
+    long long pick = 0;
+    if (lane == sel) {
+        pick = lo + (long long)s1;
+        CompF run = ex;
+        for (uint32_t i = s0; i <= s1; ++i) {
+            run = comp_add(run, CompF{weight(i), 0.f});
+            if (run.hi + run.lo >= thr) {
+                pick = lo + (long long)i;
+                break;
+            }
+        }
+    }
+    return __shfl_sync(full, pick, sel);
+}
+
+// Heat-bath decisions of a level are made either by lanes (one variable per
+// thread, rounds of tpr variables) or by warps (one variable per warp, its
+// candidates split over the lanes, rounds of tpr / 32 variables), whichever
+// costs fewer candidate evaluations per thread for the level's width `w`:
+// lane mode walks up to 3 n candidates (n = max u - l + 1; about n with the
+// closed-form windows of float QUIO below 256 values), warp mode about 6 n / 32
+// plus the fixed cost of a decision.  Every thread of a group takes the same
+// choice.
+__device__ __forceinline__ bool hb_warp_mode(int w, int tpr, uint32_t max_width, bool small_path) {
+    const float n = (float)max_width + 1.f;
+    if (n < 32.f) return false;
+    const int W = tpr >> 5;
+    const float lane_cost = (float)((w + tpr - 1) / tpr) * (small_path ? 1.f : 3.f) * n;
+    const float warp_cost = (float)((w + W - 1) / W) * (6.f * n / 32.f + 160.f);
+    return warp_cost < lane_cost;
 }
 
 // Float QUIO with at most 256 values: dE(dz) = dz (c1 + d dz), dz = v - z,
@@ -948,8 +1068,10 @@ __device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot,
     float dacc = 0.f;  // float models: energy changes since the last fold into eacc
     int gl3 = 0;  // level counter mod 3: which cooperative-list counter is live
 
-    // Decision for one record (reads replica state only).
-    auto decide = [&](const LevelRec& rc, int s, float beta, float ratio, long long& z, long long& v, F& de) {
+    // Decision for one record (reads replica state only).  With `wmode` the 32
+    // lanes of a warp call it together for the same record (heat bath only).
+    auto decide = [&](const LevelRec& rc, int s, float beta, float ratio, long long& z, long long& v, F& de,
+                      bool wmode) {
         const int k = rc.k;
         const long long lo = rc.lo;
         const long long zo = (long long)zs[k];
@@ -971,6 +1093,8 @@ __device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot,
         if constexpr (RULE == RULE_HEAT_BATH) {
             if (vv.linear()) {
                 v = heat_bath_linear(Num<F>::to_f(vv.lin_coef()), lo, rc.width, x.x0, beta);
+            } else if (wmode) {
+                v = heat_bath_warp<F, KIND>(vv, z, lo, rc.width, x.x0, beta, t & 31);
             } else {
                 bool done = false;
                 if constexpr (Num<F>::is_float && KIND == KIND_QUIO) {
@@ -1057,13 +1181,20 @@ __device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot,
             // the next level (the first level of the next sweep after the last)
             if (L + 1 < m.n_levels) prefetch_level(L + 1);
             else if (s + 1 < a.S) prefetch_level(0);
-            // every thread of the group runs the same number of rounds, so that a
-            // warp can share the neighbour updates of its accepting lanes
-            const int rounds = (le - lb + tpr - 1) / tpr;
+            // every thread of a warp runs the same number of rounds, so that the
+            // warp can share the neighbour updates of its accepting lanes; heat
+            // bath over wide ranges or narrow levels gives each variable a warp
             const int lane = t & 31;
             const bool solo = le - lb == 1;
+            bool wmode = false;
+            if constexpr (RULE == RULE_HEAT_BATH)
+                wmode = hb_warp_mode(le - lb, tpr, m.max_width,
+                                     Num<F>::is_float && KIND == KIND_QUIO && m.max_width < 256u);
+            const int per_round = wmode ? (tpr >> 5) : tpr;
+            const int slot_i = wmode ? (t >> 5) : t;
+            const int rounds = (le - lb + per_round - 1) / per_round;
             for (int rd = 0; rd < rounds; ++rd) {
-                const int i = lb + t + rd * tpr;
+                const int i = lb + slot_i + rd * per_round;
                 bool coop = false;
                 int rb = 0, rl = 0;
                 long long rdz = 0;
@@ -1071,42 +1202,60 @@ __device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot,
                     const LevelRec rc = load_rec(i);
                     long long zz, vv2;
                     F d2;
-                    decide(rc, s, beta, ratio, zz, vv2, d2);
-                    apply(rc, s, zz, vv2, d2, cnt_now, coop);
-                    rb = rc.link_begin;
-                    rl = rc.link_len;
-                    rdz = vv2 - zz;
+                    decide(rc, s, beta, ratio, zz, vv2, d2, wmode);
+                    if (!wmode || lane == 0) {
+                        apply(rc, s, zz, vv2, d2, cnt_now, coop);
+                        rb = rc.link_begin;
+                        rl = rc.link_len;
+                        rdz = vv2 - zz;
+                    }
                 }
                 if constexpr (KIND == KIND_QUIO) {
-                    // Sect. 3.2 update of the accepted rows, one row at a time, one
-                    // entry per lane (coalesced row reads, parallel atomics)
+                    // Sect. 3.2 update of the accepted rows (coalesced row reads,
+                    // parallel atomics)
                     unsigned pend = __ballot_sync(0xffffffffu, coop);
                     if (__popc(pend) > 4) {
                         // many accepting lanes: each updates its own row
                         if (coop) quio_update_row<F>(m, cache, rb, rl, rdz);
                         pend = 0;
                     }
-                    while (pend) {
-                        const int src = __ffs(pend) - 1;
-                        pend &= pend - 1;
-                        const int b = __shfl_sync(0xffffffffu, rb, src);
-                        const int l = __shfl_sync(0xffffffffu, rl, src);
-                        const long long dz = __shfl_sync(0xffffffffu, rdz, src);
-                        if (solo) {
-                            // the level's only variable: its row's columns are
-                            // distinct and nothing else touches the cache now
-                            for (int e = lane; e < l; e += 32) {
-                                if constexpr (Num<F>::is_float)
-                                    cache[__ldg(m.adj_col + b + e)] += __ldg(m.adj_f + b + e) * (float)(int)dz;
-                                else
-                                    cache[m.adj_col[b + e]] += m.adj_i[b + e] * dz;
+                    // up to 4 accepting lanes: their rows are walked together, one
+                    // entry per lane, with every row's loads issued before the
+                    // atomics, so that the L2 latency is paid once per round
+                    if (pend) {
+                        int b4[4], l4[4], lmax = 0;
+                        long long dz4[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int src = pend ? __ffs(pend) - 1 : 0;
+                            const bool on = pend != 0u;
+                            pend &= pend - 1;
+                            b4[j] = __shfl_sync(0xffffffffu, rb, src);
+                            l4[j] = on ? __shfl_sync(0xffffffffu, rl, src) : 0;
+                            dz4[j] = __shfl_sync(0xffffffffu, rdz, src);
+                            lmax = max(lmax, l4[j]);
+                        }
+                        for (int e0 = 0; e0 < lmax; e0 += 32) {
+                            int col4[4];
+                            F w4[4];
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                if (e0 + lane < l4[j]) {
+                                    col4[j] = __ldg(m.adj_col + b4[j] + e0 + lane);
+                                    w4[j] = Coef<F>::adj(m, b4[j] + e0 + lane);
+                                }
                             }
-                        } else {
-                            for (int e = lane; e < l; e += 32) {
-                                if constexpr (Num<F>::is_float)
-                                    atomic_add_field(cache + __ldg(m.adj_col + b + e), __ldg(m.adj_f + b + e) * (float)(int)dz);
-                                else
-                                    atomic_add_field(cache + m.adj_col[b + e], m.adj_i[b + e] * dz);
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                if (e0 + lane < l4[j]) {
+                                    F inc;
+                                    if constexpr (Num<F>::is_float) inc = w4[j] * (float)(int)dz4[j];
+                                    else inc = w4[j] * dz4[j];
+                                    // a level's only variable: its row's columns are
+                                    // distinct and nothing else touches the cache now
+                                    if (solo) cache[col4[j]] += inc;
+                                    else atomic_add_field(cache + col4[j], inc);
+                                }
                             }
                         }
                     }

@@ -235,6 +235,26 @@ def random_interaction(n: int, p: int, u: int, n_terms: int = 1000, seed: int = 
     return _pack(n, np.full(n, -u), np.full(n, u), idx.tolist(), J, "f64")
 
 
+def quartic_wells(seed: int, n: int = 24, u: int = 1000):
+    """Integer HUIO with one tilted double well per variable over z in [-u, u]:
+    a_k z^4 - 2 a_k w_k^2 z^2 + c_k z^3 + h_k z (a_k in {1,2,3}, w_k in
+    [u/5, 9u/10]), coupled along a ring by J z_i z_j, z_i^2 z_j and z_i^2 z_j^2
+    terms.  Every variable's energy difference is a quartic polynomial with up
+    to two interior minima, so optimal-transition proposals need the full
+    degree-4 argmin and heat-bath draws span 2u + 1 values."""
+    rng = np.random.default_rng(seed)
+    terms, coefs = [], []
+    for k in range(n):
+        a = int(rng.integers(1, 4))
+        w = int(rng.integers(u // 5, 9 * u // 10 + 1))
+        terms += [[k] * 4, [k] * 2, [k] * 3, [k]]
+        coefs += [a, -2 * a * w * w, int(rng.integers(-u // 2, u // 2 + 1)), int(rng.integers(-10 ** 8, 10 ** 8 + 1))]
+        j = (k + 1) % n
+        terms += [[k, j], [k, k, j], [k, k, j, j]]
+        coefs += [int(rng.integers(-10 ** 5, 10 ** 5 + 1)), int(rng.integers(-100, 101)), int(rng.integers(-1, 2))]
+    return _pack(n, np.full(n, -u), np.full(n, u), terms, coefs, "i64")
+
+
 def random_small(seed: int, n: int, max_order: int, lo, hi, n_terms: int,
                  coef_type: str = "i32", cmax: int = 5, repeat: bool = True,
                  with_linear: bool = True):

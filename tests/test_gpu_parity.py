@@ -10,6 +10,7 @@ an FP64 recomputation, and final-energy distributions over replicas equal to
 the oracle's by a two-sample KS test at p > 0.01.
 """
 import concurrent.futures as cf
+import os
 
 import numpy as np
 import pytest
@@ -38,7 +39,10 @@ def _device_run(model, rule, S, R, seed, tmax, tmin, trace_R=0, **kw):
     return res
 
 
-def _oracle_follow(om, rule, S, seed, tmax, tmin, replicas, trace, trace_R, workers=8):
+WORKERS = max(4, os.cpu_count() or 4)
+
+
+def _oracle_follow(om, rule, S, seed, tmax, tmin, replicas, trace, trace_R, workers=WORKERS):
     def one(r):
         return om.run(rule, S, seed, tmax, tmin, r_begin=r, r_end=r + 1, trace=trace, trace_replicas=trace_R,
                       margin=MARGIN)
@@ -98,6 +102,28 @@ def test_huio_random_interaction_powers(rule):
 
 
 @pytest.mark.parametrize("rule", ALL_RULES)
+def test_huio_random_interaction_u100(rule):
+    """E^RI_{4,100} (Sect. 4) with integer J: exponents up to 4 over 201 values
+    per variable.  Every attempt is replayed against the oracle, whose OTM
+    proposal is the brute-force argmin over all 200 changes, so the degree-3/4
+    bracketing of the kernel's argmin is checked wherever a proposal is taken."""
+    inst = wl.random_interaction(60, 4, 100, n_terms=1000, seed=5, integer=True, int_scale=50)
+    S = {"metropolis": 300, "heat_bath": 40, "opt_metropolis": 150}[rule]
+    _check_int_parity(inst, rule, S, 16, 5, 6, label="RI p=4 u=100")
+
+
+@pytest.mark.parametrize("rule", ALL_RULES)
+def test_huio_quartic_wells_wide(rule):
+    """Tilted double wells a z^4 - 2 a w^2 z^2 + c z^3 + h z over [-1000, 1000],
+    ring-coupled: quartic energy differences with two interior minima (OTM
+    argmin against brute force over 2000 changes) and heat-bath draws over 2001
+    values, replayed attempt by attempt."""
+    inst = wl.quartic_wells(3)
+    S = {"metropolis": 400, "heat_bath": 60, "opt_metropolis": 300}[rule]
+    _check_int_parity(inst, rule, S, 24, 7, 8, label="quartic wells +-1000")
+
+
+@pytest.mark.parametrize("rule", ALL_RULES)
 def test_huio_multilinear_closed_form(rule):
     """Multilinear model (heat bath via the O(1) inverse transform)."""
     inst = wl.multilinear(50, 3, 7, integer=True)
@@ -142,7 +168,7 @@ def _float_check(inst, rule, S, R, seed, R_oracle, refresh=0):
     sts = st.cpu().numpy()
     e_orc_of_dev = np.array([om.energy(sts[r]) for r in range(min(R, 64))])
     np.testing.assert_allclose(e_dev[:len(e_orc_of_dev)], e_orc_of_dev, rtol=1e-5, atol=1e-6)
-    with cf.ThreadPoolExecutor(max_workers=8) as ex:
+    with cf.ThreadPoolExecutor(max_workers=WORKERS) as ex:
         res = list(ex.map(lambda r: om.run(rule, S, seed, tmax, tmin, r_begin=r, r_end=r + 1), range(R_oracle)))
     e_orc = np.array([x["energy"][0] for x in res])
     p = stats.ks_2samp(e_dev, e_orc).pvalue
@@ -156,6 +182,18 @@ def _float_check(inst, rule, S, R, seed, R_oracle, refresh=0):
 def test_quio_float_statistical(rule):
     inst = wl.quio_sparse_wide(11, n=1500, n_edges=12000, lo=0, hi=63)
     _float_check(inst, rule, 100, 512, 3, 96, refresh=25)
+
+
+@pytest.mark.parametrize("rule", ALL_RULES)
+def test_quio_float_wide_range_statistical(rule):
+    """Float QUIO over [0,255], the benchmarked range (reduced N = 1500, 12,000
+    edges): heat bath through the closed-form window and the register block
+    sums (vertex inside, below and above the range), OTM through the quadratic
+    vertex, with FP64 refreshes every 10 sweeps; 512 device replicas against 96
+    oracle replicas."""
+    inst = wl.quio_sparse_wide(11, n=1500, n_edges=12000, lo=0, hi=255)
+    S = 100 if rule == "metropolis" else 40
+    _float_check(inst, rule, S, 512, 3, 96, refresh=10)
 
 
 @pytest.mark.parametrize("rule", ALL_RULES)
@@ -230,8 +268,9 @@ def test_init_states_and_host_outputs():
     inst = wl.huio_zipf(6, n=120, n_quad=200, n_cubic=200, n_quartic=50, lo=-4, hi=4)
     model = Model(inst)
     init = wl.initial_states(1, inst, 8)
+    trace = torch.zeros((30, 8, model.n), dtype=torch.int32, device="cuda")
     dev_out = model.run("opt_metropolis", 30, 8, seed=2, t_max=50.0, t_min=0.5,
-                        init_states=torch.from_numpy(init).cuda())
+                        init_states=torch.from_numpy(init).cuda(), trace=trace, trace_replicas=8)
     hs = np.zeros((8, model.n), np.int32)
     he = np.zeros(8, np.int64)
     ha = np.zeros(8, np.uint64)
@@ -240,21 +279,27 @@ def test_init_states_and_host_outputs():
     assert np.array_equal(hs, dev_out["states"].cpu().numpy())
     assert np.array_equal(he, dev_out["energies"].cpu().numpy())
     om = orc.Model(inst)
-    x = om.run("opt_metropolis", 30, 2, 50.0, 0.5, r_begin=0, r_end=8, init_states=init)
-    if x["follow"]["near_threshold"] == 0:
-        assert np.array_equal(x["states"], hs)
+    x = om.run("opt_metropolis", 30, 2, 50.0, 0.5, r_begin=0, r_end=8, init_states=init,
+               trace=trace.cpu().numpy(), trace_replicas=8)
+    assert x["follow"]["mismatch"] == 0, x["follow"]
+    assert np.array_equal(x["states"], hs)
+    assert np.array_equal(x["energy"], he)
+    assert np.array_equal(x["changes"], ha.astype(np.int64))
 
 
 def test_energy_trace_matches_final():
     inst = wl.quio_dense_small(1)
     model = Model(inst)
     et = torch.zeros((25, 10), dtype=torch.int64, device="cuda")
-    out = model.run("metropolis", 25, 10, seed=3, t_max=50.0, t_min=0.5, energy_trace=et)
+    trace = torch.zeros((25, 10, model.n), dtype=torch.int32, device="cuda")
+    out = model.run("metropolis", 25, 10, seed=3, t_max=50.0, t_min=0.5, energy_trace=et, trace=trace,
+                    trace_replicas=10)
     assert torch.equal(et[-1], out["energies"])
     om = orc.Model(inst)
-    x = om.run("metropolis", 25, 3, 50.0, 0.5, r_begin=0, r_end=10, energy_trace=True)
-    if x["follow"]["near_threshold"] == 0:
-        assert np.array_equal(x["energy_trace"], et.cpu().numpy())
+    x = om.run("metropolis", 25, 3, 50.0, 0.5, r_begin=0, r_end=10, energy_trace=True,
+               trace=trace.cpu().numpy(), trace_replicas=10)
+    assert x["follow"]["mismatch"] == 0, x["follow"]
+    assert np.array_equal(x["energy_trace"], et.cpu().numpy())
 
 
 def test_errors():

@@ -10,6 +10,7 @@ from scipy import stats
 
 torch = pytest.importorskip("torch")
 
+from oracle import oracle as orc
 from paper_2511_17245_gb300 import (Model, SAError, make_params, sa_server_cancel, sa_server_create,
                                     sa_server_destroy, sa_server_get_stats, sa_server_poll, sa_server_result,
                                     sa_server_submit, sa_server_wait)
@@ -80,6 +81,30 @@ def test_alone_equals_in_mix():
         one = m.run(sp["rule"], sp["sweeps"], sp["replicas"], seed=sp["seed"], instance_id=sp["index"],
                     t_max=p.t_max, t_min=p.t_min)
         assert np.array_equal(one["states"].cpu().numpy(), alone[k][0])
+    # and, for the two cheapest integer requests of the mix, equal to the CPU
+    # oracle: the traced replicas of a direct run are replayed attempt by
+    # attempt (decisions within 1e-6 of a threshold follow the trace), and the
+    # served rows must equal the oracle's final states, energies and changes
+    ints = sorted((k for k in byidx if not models[k].is_float),
+                  key=lambda k: byidx[k]["n"] * byidx[k]["sweeps"] * (2000 if byidx[k]["rule"] != "metropolis" else 1))
+    assert len(ints) >= 2
+    for k in ints[:2]:
+        m, sp = models[k], byidx[k]
+        p = _params(m, sp)
+        inst = wl.serving_instance(sp)
+        om = orc.Model(inst)
+        S, TR = sp["sweeps"], 2
+        trace = torch.zeros((S, TR, m.n), dtype=torch.int32, device="cuda")
+        m.run(sp["rule"], S, sp["replicas"], seed=sp["seed"], instance_id=sp["index"], t_max=p.t_max,
+              t_min=p.t_min, trace=trace, trace_replicas=TR)
+        torch.cuda.synchronize()
+        x = om.run(sp["rule"], S, sp["seed"], p.t_max, p.t_min, r_begin=0, r_end=TR, instance=sp["index"],
+                   trace=trace.cpu().numpy(), trace_replicas=TR)
+        assert x["follow"]["mismatch"] == 0, (k, x["follow"])
+        st, en, ac = mix[k]
+        assert np.array_equal(x["states"], st[:TR]), k
+        assert np.array_equal(x["energy"], en[:TR]), k
+        assert np.array_equal(x["changes"], ac[:TR].astype(np.int64)), k
 
 
 def test_budget_admission_and_backfill():

@@ -105,3 +105,49 @@ def test_plan_schedule_closed_form(tmp_path):
     tmax, tmin = -3.0 / np.log(0.5), -2.0 / np.log(0.001)
     assert out[14] == np.float32(1 / tmax) and out[15] == np.float32(1 / tmin) and out[16] == 1
     assert out[17:19] == [1, 1]
+
+
+@pytest.mark.parametrize("R,S,P", [(1024, 100, 608), (1024, 7, 608), (700, 50, 608), (609, 3, 608),
+                                   (5000, 20, 152), (61, 13, 60), (10, 1, 3), (608, 9, 608)])
+def test_slice_plan_covers_every_sweep_once(tmp_path, R, S, P):
+    """Time-sliced schedule: every (replica, sweep) pair is run by exactly one
+    slot, each replica's pieces are contiguous and in sweep order, a split
+    replica's head is the last piece group of slot p and its tail the first of
+    slot p + 1, and the head ends no later (in the slot's own sweep count)
+    than the tail starts."""
+    Q = -(-R * S // P)
+    body = f"""
+  for (int p = 0; p < {P}; ++p) {{
+    sa::SlicePlan sp = sa::slice_plan(p, {R}, {S}, {P}LL);
+    std::printf("%d %d %d %d %d %d %d %d %d %d %d\\n", p, sp.has_head, sp.head.r, sp.head.s0, sp.head.s1,
+                sp.whole_r0, sp.whole_r1, sp.has_tail, sp.tail.r, sp.tail.s0, sp.tail.s1);
+  }}
+"""
+    out = [int(x) for x in _compile_and_run(tmp_path, body)]
+    rows = [out[i:i + 11] for i in range(0, 11 * P, 11)]
+    seen = {}
+    for p, hh, hr, h0, h1, w0, w1, ht, tr, t0, t1 in rows:
+        order = []          # the slot's own execution order: head, whole, tail
+        if hh:
+            order.append((hr, h0, h1))
+        order += [(r, 0, S) for r in range(w0, w1)]
+        if ht:
+            order.append((tr, t0, t1))
+        assert sum(b - a for _, a, b in order) <= Q
+        clock = 0
+        for r, a, b in order:
+            assert 0 <= a < b <= S
+            for s in range(a, b):
+                assert (r, s) not in seen
+                seen[(r, s)] = (p, clock + (s - a))
+            clock += b - a
+    assert len(seen) == R * S
+    for r in range(R):
+        slots = [seen[(r, s)] for s in range(S)]
+        ps = sorted({x[0] for x in slots})
+        assert len(ps) <= 2 and (len(ps) == 1 or ps[1] == ps[0] + 1)
+        if len(ps) == 2:
+            # head on ps[0] (sweeps 0..), tail on ps[1]; head finishes before the tail starts
+            head = [t for (p, t) in slots if p == ps[0]]
+            tail = [t for (p, t) in slots if p == ps[1]]
+            assert slots[0][0] == ps[0] and max(head) < min(tail)

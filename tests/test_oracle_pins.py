@@ -325,8 +325,11 @@ def test_heat_bath_closed_form_multilinear():
 def _python_sa(inst, rule, n_sweeps, seed, t_max, t_min, replica):
     """Independent plain-Python SA of Sect. 3 on a tiny instance: full-energy
     recomputation for every candidate, paper's rules, the documented random
-    conventions (Philox counters, 24-bit uniforms, multiply-shift picks)."""
+    conventions (Philox counters, 24-bit uniforms, multiply-shift picks).
+    Returns the final state, the number of near-threshold decisions and the
+    value of z_k after every attempt ([S][N])."""
     n = inst["n_vars"]
+    trace = np.zeros((n_sweeps, n), np.int32)
     lo, hi = inst["lower"], inst["upper"]
     key = [seed & 0xFFFFFFFF, seed >> 32]
 
@@ -369,6 +372,7 @@ def _python_sa(inst, rule, n_sweeps, seed, t_max, t_min, replica):
                         pick = v
                         break
                 z[k] = pick
+                trace[s, k] = z[k]
                 continue
             if rule == "opt_metropolis" and np.float32((w[2] >> 8) * 2.0 ** -24) < ratio:
                 cands = [v for v in range(int(lo[k]), int(hi[k]) + 1) if v != z[k]]
@@ -380,6 +384,7 @@ def _python_sa(inst, rule, n_sweeps, seed, t_max, t_min, replica):
             d = dE(prop)
             if d <= 0:
                 z[k] = prop
+                trace[s, k] = z[k]
                 continue
             p = float(np.exp(-(np.float32(d) * beta), dtype=np.float32))
             U = (w[1] >> 8) * 2.0 ** -24
@@ -387,7 +392,8 @@ def _python_sa(inst, rule, n_sweeps, seed, t_max, t_min, replica):
                 near += 1
             if U < p:
                 z[k] = prop
-    return np.array(z), near
+            trace[s, k] = z[k]
+    return np.array(z), near, trace
 
 
 @pytest.mark.parametrize("rule", ["metropolis", "heat_bath", "opt_metropolis"])
@@ -397,10 +403,20 @@ def test_run_matches_independent_python_sa(rule):
     inst = wl.random_small(41, n=4, max_order=3, lo=-2, hi=3, n_terms=12, coef_type="i32", cmax=4)
     m = orc.Model(inst)
     for rep in range(3):
-        res = m.run(rule, 12, seed=0x1234_0000_0042, t_max=20.0, t_min=0.5, r_begin=rep, r_end=rep + 1)
-        z_py, near = _python_sa(inst, rule, 12, 0x1234_0000_0042, 20.0, 0.5, rep)
-        if near == 0:
-            assert res["states"][0].tolist() == z_py.tolist()
+        z_py, near, tr = _python_sa(inst, rule, 12, 0x1234_0000_0042, 20.0, 0.5, rep)
+        # the oracle replays the Python trajectory, adopting its decision only
+        # within the 1e-6 margin of a threshold; any other difference counts
+        follow = np.zeros((12, rep + 1, inst["n_vars"]), np.int32)
+        follow[:, rep, :] = tr
+        res = m.run(rule, 12, seed=0x1234_0000_0042, t_max=20.0, t_min=0.5, r_begin=rep, r_end=rep + 1,
+                    trace=follow, trace_replicas=rep + 1)
+        assert res["follow"]["mismatch"] == 0, res["follow"]
+        assert res["states"][0].tolist() == z_py.tolist()
+        # these seeds meet no decision within the margin, so the oracle's own
+        # run (no following) reproduces the Python trajectory as well
+        assert near == 0 and res["follow"]["followed"] == 0
+        own = m.run(rule, 12, seed=0x1234_0000_0042, t_max=20.0, t_min=0.5, r_begin=rep, r_end=rep + 1)
+        assert own["states"][0].tolist() == z_py.tolist()
 
 
 @pytest.mark.parametrize("rule", ["metropolis", "heat_bath", "opt_metropolis"])
