@@ -213,15 +213,21 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- growth directions
-def run_batched_vs_plain(torch, sample_every=128):
+def run_batched_vs_plain(torch, hbm_gbs, sample_every=128, sweep_grid=(250, 500, 1000)):
     """4,096 uneven QUIO instances (N log-uniform in [50,2000], range width
     log-uniform in [2,1024], half dense / half sparse with degree 8..64, fp32),
     32 replicas, 1000 sweeps, Metropolis, per-instance temperatures of
-    Sect. 3.4: one persistent graph-captured launch (autotuned shape) vs the
-    plain form (one sa_run launch per instance, serialised on one stream),
-    timed on every `sample_every`-th instance and scaled up.  Both forms use the
-    same Philox counters, so their final energies agree (same quality); the
-    time-to-target energy of each form is its time to produce those energies."""
+    Sect. 3.4.
+      batched  one persistent graph-captured launch (autotuned shape);
+      plain    one sa_run launch per instance, serialised on one stream, timed
+               on every `sample_every`-th dense and sparse instance and scaled;
+      time to target  target E* = sum over instances of the plain form's mean
+               final energy at 1000 sweeps (same seeds); the batched form is
+               run at each sweep count of `sweep_grid` and its time to target
+               is the time of the first count whose energy sum is <= E*;
+      dense half  the 2,048 dense instances as their own batch: HBM fraction
+               of their J-row reads (one row of N-1 (column, value) pairs, 8 B
+               each, per accepted change, counted from the change counts)."""
     import concurrent.futures as cf
     from paper_2511_17245_gb300 import (Model, make_params, sa_batch_autotune, sa_batch_create, sa_batch_destroy,
                                         sa_batch_get_info, sa_batch_result, sa_batch_run, sa_run)
@@ -232,84 +238,141 @@ def run_batched_vs_plain(torch, sample_every=128):
         insts = list(ex.map(wl.batch_instance, specs))
     with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
         models = list(ex.map(Model, insts))
+    del insts
     create_s = time.perf_counter() - t0
-    params = []
-    for i, m in enumerate(models):
-        tmax, tmin = m.default_temperatures()
-        params.append(make_params("metropolis", 1000, 32, seed=0, instance_id=i, t_max=tmax, t_min=tmin))
+    temps = [m.default_temperatures() for m in models]
     st = torch.cuda.current_stream()
-    b = sa_batch_create([m.handle for m in models], params)
-    try:
-        sa_batch_autotune(b, 10, st.cuda_stream)
-        info = sa_batch_get_info(b)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        sa_batch_run(b, st.cuda_stream)
-        e1.record(st)
-        torch.cuda.synchronize()
-        batched_ms = e0.elapsed_time(e1)
-        # stratified: instances alternate dense / sparse, so take every
-        # sample_every-th instance of each class
-        sample = list(range(0, len(models), sample_every)) + list(range(1, len(models), sample_every))
-        plain_ms, rel = 0.0, []
-        for i in sample:
-            m, p = models[i], params[i]
-            o_s = torch.empty((32, m.n), dtype=torch.int32, device="cuda")
-            o_e = torch.empty(32, dtype=torch.float64, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def params_for(S, idx):
+        return [make_params("metropolis", S, 32, seed=0, instance_id=i, t_max=temps[i][0], t_min=temps[i][1])
+                for i in idx]
+
+    def timed_batch(idx, S, tune):
+        b = sa_batch_create([models[i].handle for i in idx], params_for(S, idx))
+        try:
+            if tune:
+                sa_batch_autotune(b, 10, st.cuda_stream)
+            info = sa_batch_get_info(b)
             e0.record(st)
-            sa_run(m.handle, p, o_s, o_e, None, st.cuda_stream)
+            sa_batch_run(b, st.cuda_stream)
             e1.record(st)
             torch.cuda.synchronize()
-            plain_ms += e0.elapsed_time(e1)
-            be = np.zeros(32, np.float64)
-            sa_batch_result(b, i, None, be, None)
-            pe = o_e.cpu().numpy()
-            rel.append(abs(be.mean() - pe.mean()) / max(1e-12, abs(pe.mean())))
-        plain_total_ms = plain_ms * len(models) / len(sample)
-        att = info["attempts"]
-        return {"workload": "4096 uneven QUIO instances, 32 replicas, 1000 sweeps, metropolis",
-                "model_create_s": create_s, "batched_ms": batched_ms, "batched_attempts_per_s": att / (batched_ms / 1e3),
-                "plain_ms_estimated": plain_total_ms, "plain_attempts_per_s": att / (plain_total_ms / 1e3),
-                "plain_sample": f"every {sample_every}th instance ({len(sample)} launches), scaled by {len(models) / len(sample):.0f}",
-                "speedup": plain_total_ms / batched_ms,
-                "time_to_target_ms": {"batched": batched_ms, "plain": plain_total_ms},
-                "final_energy_mean_rel_diff_max": float(max(rel)), "launch_shape": info}
-    finally:
-        sa_batch_destroy(b)
+            ms = e0.elapsed_time(e1)
+            en = np.zeros((len(idx), 32), np.float64)
+            acc = np.zeros((len(idx), 32), np.uint64)
+            for j in range(len(idx)):
+                sa_batch_result(b, j, None, en[j], acc[j])
+            return ms, en, acc, info
+        finally:
+            sa_batch_destroy(b)
+
+    _progress(f"batched: {len(models)} models built in {create_s:.1f} s")
+    everyone = list(range(len(models)))
+    grid = {}
+    for S in sweep_grid:
+        ms, en, acc, info = timed_batch(everyone, S, tune=True)
+        _progress(f"batched: {S} sweeps {ms:.0f} ms")
+        grid[S] = {"ms": ms, "energy_sum": float(en.mean(axis=1).sum()), "attempts": info["attempts"],
+                   "launch_shape": {k: info[k] for k in ("threads_per_replica", "replicas_per_block", "blocks")}}
+        if S == 1000:
+            en1000 = en
+    batched_ms = grid[1000]["ms"]
+    att = grid[1000]["attempts"]
+    # plain form on a stratified sample (instances alternate dense / sparse)
+    sample = list(range(0, len(models), sample_every)) + list(range(1, len(models), sample_every))
+    plain_ms, rel = 0.0, []
+    for i in sample:
+        m, p = models[i], params_for(1000, [i])[0]
+        o_s = torch.empty((32, m.n), dtype=torch.int32, device="cuda")
+        o_e = torch.empty(32, dtype=torch.float64, device="cuda")
+        e0.record(st)
+        sa_run(m.handle, p, o_s, o_e, None, st.cuda_stream)
+        e1.record(st)
+        torch.cuda.synchronize()
+        plain_ms += e0.elapsed_time(e1)
+        pe = o_e.cpu().numpy()
+        rel.append(abs(en1000[i].mean() - pe.mean()) / max(1e-12, abs(pe.mean())))
+    plain_total_ms = plain_ms * len(models) / len(sample)
+    _progress(f"batched: plain sample {plain_ms:.0f} ms")
+    target = grid[1000]["energy_sum"]   # equal to the plain form's (same seeds; checked on the sample)
+    ttt = next(grid[S]["ms"] for S in sweep_grid if grid[S]["energy_sum"] <= target)
+    # dense half alone: HBM roofline of its J-row reads
+    dense = [i for i in everyone if specs[i]["dense"]]
+    dms, _, dacc, _ = timed_batch(dense, 1000, tune=True)
+    row_bytes = sum(float(dacc[j].sum()) * (models[i].n - 1) * 8 for j, i in enumerate(dense))
+    dense_gbs = row_bytes / (dms / 1e3) / 1e9
+    for m in models:
+        m.close()
+    return {"workload": "4096 uneven QUIO instances, 32 replicas, 1000 sweeps, metropolis",
+            "model_create_s": create_s, "batched_ms": batched_ms, "batched_attempts_per_s": att / (batched_ms / 1e3),
+            "plain_ms_estimated": plain_total_ms, "plain_attempts_per_s": att / (plain_total_ms / 1e3),
+            "plain_sample": f"every {sample_every}th dense and sparse instance ({len(sample)} launches), "
+                            f"scaled by {len(models) / len(sample):.0f}",
+            "speedup": plain_total_ms / batched_ms,
+            "time_to_target_ms": {"batched": ttt, "plain": plain_total_ms,
+                                  "target": "sum of per-instance mean final energies of the plain form, 1000 sweeps",
+                                  "batched_sweep_grid": {str(S): {"ms": grid[S]["ms"], "energy_sum": grid[S]["energy_sum"]}
+                                                         for S in sweep_grid}},
+            "final_energy_mean_rel_diff_max": float(max(rel)), "launch_shape": grid[1000]["launch_shape"],
+            "dense_half": {"instances": len(dense), "ms": dms, "row_bytes": row_bytes, "achieved_gbs": dense_gbs,
+                           "hbm_peak_gbs": hbm_gbs, "frac": dense_gbs / hbm_gbs}}
 
 
-def run_serving(torch, n_requests=40, load=0.8, max_attempts=2e8):
-    """The first `n_requests` requests of the request stream (N log-uniform in
-    [100, 50,000], ranges up to 4096, 70% QUIO / 30% HUIO, mixed rules,
-    100-5000 sweeps, int32 or fp32 coefficients, 32 replicas) of at most
-    `max_attempts` attempts each (N x replicas x sweeps; the larger requests
-    of the stream take minutes each on 32 replicas and are left out of this
-    bounded sample) through the server with a 150 GB device budget: first all
-    requests at once (closed loop: capacity in attempts/s), then the same
-    requests with Poisson arrivals at `load` times that capacity (latency
-    percentiles)."""
-    import concurrent.futures as cf
-    from paper_2511_17245_gb300 import (Model, make_params, sa_server_create, sa_server_destroy,
-                                        sa_server_get_stats, sa_server_result, sa_server_submit, sa_server_wait)
+def _progress(msg):
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
+def serving_window(max_total_attempts=1.5e11):
+    """The prefix of the 20,000-request stream (in arrival order, every request
+    kept whatever its size) whose attempts (N x replicas x sweeps) add up to at
+    most `max_total_attempts`."""
     from paper_2511_17245_gb300 import workloads as wl
-    specs = [sp for sp in wl.serving_specs(4)
-             if sp["n"] * sp["replicas"] * sp["sweeps"] <= max_attempts][:n_requests]
+    out, tot = [], 0.0
+    for sp in wl.serving_specs(4):
+        a = sp["n"] * sp["replicas"] * sp["sweeps"]
+        if out and tot + a > max_total_attempts:
+            break
+        out.append(sp)
+        tot += a
+    return out, tot
+
+
+def run_serving(torch, load=0.8, max_total_attempts=1.5e11):
+    """Serving on a window of the request stream (N log-uniform in [100, 50,000],
+    ranges [2, 4096], 70% QUIO / 30% HUIO, rules uniform, 100-5000 sweeps, int32
+    or fp32 coefficients, 32 replicas): the first requests of the stream in
+    order, up to `max_total_attempts` attempts in all.  Through the server
+    (150 GB budget, one persistent kernel draining a shared unit queue): all
+    requests at once (closed loop: capacity), then Poisson arrivals at `load`
+    times that capacity (latency percentiles).  The same requests through the
+    batched form (one persistent graph launch per rule / model kind /
+    coefficient class group, groups one after another) for comparison, with
+    the integer requests' results checked equal between the two forms."""
+    import concurrent.futures as cf
+    from paper_2511_17245_gb300 import (Model, make_params, sa_batch_create, sa_batch_destroy, sa_batch_result,
+                                        sa_batch_run, sa_server_create, sa_server_destroy, sa_server_get_stats,
+                                        sa_server_result, sa_server_submit, sa_server_wait)
+    from paper_2511_17245_gb300 import workloads as wl
+    specs, total_att = serving_window(max_total_attempts)
     t0 = time.perf_counter()
     with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
         insts = list(ex.map(wl.serving_instance, specs))
     with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
         models = list(ex.map(Model, insts))
+    del insts
     create_s = time.perf_counter() - t0
     params = []
     for sp, m in zip(specs, models):
         tmax, tmin = m.default_temperatures()
         params.append(make_params(sp["rule"], sp["sweeps"], sp["replicas"], seed=sp["seed"], instance_id=sp["index"],
                                   t_max=tmax, t_min=tmin))
-    mean_att = float(np.mean([sp["n"] * sp["replicas"] * sp["sweeps"] for sp in specs]))
+    mean_att = total_att / len(specs)
+    served = {}
 
-    def one_pass(rate):
+    def one_pass(rate, keep):
         rng = np.random.default_rng(7)
-        srv = sa_server_create(150 << 30, n_streams=64)
+        srv = sa_server_create(150 << 30, max_running=4096)
         try:
             tickets = []
             start = time.perf_counter()
@@ -321,29 +384,77 @@ def run_serving(torch, n_requests=40, load=0.8, max_attempts=2e8):
                     if delay > 0:
                         time.sleep(delay)
                 tickets.append(sa_server_submit(srv, m.handle, p))
-            for t in tickets:
+            for i, t in enumerate(tickets):
                 sa_server_wait(srv, t, 3_600_000_000)
-                sa_server_result(srv, t)
+                if keep and not models[i].is_float:
+                    en = np.zeros(params[i].n_replicas, np.int64)
+                    sa_server_result(srv, t, None, en, None)
+                    served[i] = en
+                else:
+                    sa_server_result(srv, t)
             return sa_server_get_stats(srv)
         finally:
             sa_server_destroy(srv)
 
-    closed = one_pass(None)
+    _progress(f"serving: {len(specs)} models built in {create_s:.1f} s")
+    closed = one_pass(None, True)
+    _progress(f"serving: closed loop {closed['attempts_per_s']:.3g} attempts/s")
     rate = load * closed["attempts_per_s"] / mean_att
-    open_ = one_pass(rate)
-    return {"workload": f"first {len(specs)} requests of at most {max_attempts:.0e} attempts of the "
-                        f"20,000-request stream ({sum(sp['n'] * sp['replicas'] * sp['sweeps'] for sp in specs):.3g} "
-                        f"attempts)", "model_create_s": create_s,
+    open_ = one_pass(rate, False)
+    _progress(f"serving: Poisson pass done, p99 {open_['p99_latency_ms']:.0f} ms")
+
+    # batched form on the same requests: one batch per rule, model kind,
+    # coefficient class and state placement (a batch keeps all its states in
+    # shared memory or all in global memory, so requests whose state does not
+    # fit on chip form batches of their own)
+    groups = {}
+    for i, (sp, m) in enumerate(zip(specs, models)):
+        big = m.n * (2 + (4 if m.is_float else 8)) * (1 if m.info["is_quadratic"] else 2) > 48 * 1024
+        key = (sp["rule"], bool(m.info["is_quadratic"]), m.is_float, big)
+        groups.setdefault(key, []).append(i)
+    st = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    batched_ms, mismatch, checked = 0.0, 0, 0
+    for key, idx in groups.items():
+        b = sa_batch_create([models[i].handle for i in idx], [params[i] for i in idx])
+        try:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            sa_batch_run(b, st.cuda_stream)
+            e1.record(st)
+            torch.cuda.synchronize()
+            batched_ms += e0.elapsed_time(e1)
+            for j, i in enumerate(idx):
+                if i in served:
+                    en = np.zeros(params[i].n_replicas, np.int64)
+                    sa_batch_result(b, j, None, en, None)
+                    checked += 1
+                    mismatch += int(not np.array_equal(en, served[i]))
+        finally:
+            sa_batch_destroy(b)
+        _progress(f"serving: batched group {key} ({len(idx)} requests) done")
+    batched_wall = time.perf_counter() - t0
+    for m in models:
+        m.close()
+    return {"workload": f"first {len(specs)} requests of the 20,000-request stream, in order "
+                        f"({total_att:.3g} attempts; largest N {max(sp['n'] for sp in specs)})",
+            "model_create_s": create_s,
             "closed_loop": {"attempts_per_s": closed["attempts_per_s"], "p50_latency_ms": closed["p50_latency_ms"],
-                            "p99_latency_ms": closed["p99_latency_ms"]},
+                            "p99_latency_ms": closed["p99_latency_ms"], "kernel_launches": closed["kernel_launches"]},
             "poisson": {"arrival_rate_per_s": rate, "load": load, "attempts_per_s": open_["attempts_per_s"],
                         "p50_latency_ms": open_["p50_latency_ms"], "p99_latency_ms": open_["p99_latency_ms"],
                         "completed": open_["completed"], "failed": open_["failed"],
                         "device_bytes_peak": open_["device_bytes_peak"]},
+            "batched_same_requests": {"groups": len(groups), "kernel_ms": batched_ms,
+                                      "attempts_per_s": total_att / (batched_ms / 1e3),
+                                      "wall_s_incl_create": batched_wall,
+                                      "integer_requests_equal": f"{checked - mismatch}/{checked}"},
+            "served_vs_batched": closed["attempts_per_s"] / (total_att / (batched_ms / 1e3)),
             "budget_bytes": 150 << 30}
 
 
-def run_small_configs(torch, steps=3, warmup=3):
+def run_small_configs(torch, steps=2, warmup=1):
     """The two other single-run workloads, each rule timed with CUDA events
     (median of `steps` runs after `warmup`): the dense 32-variable integer QUIO
     (z in [-8,7], 64 replicas x 1000 sweeps, T 100 -> 0.1) and the Zipf HUIO
@@ -397,10 +508,9 @@ def main():
     ap.add_argument("--replicas", type=int, default=REPLICAS,
                     help="override for profiling a smaller case (bench numbers use the default)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--small-configs", action="store_true",
-                    help="also time the dense 32-variable QUIO and the Zipf HUIO workloads")
-    ap.add_argument("--extended", action="store_true",
-                    help="also run the batched-vs-plain and serving measurements (several minutes)")
+    ap.add_argument("--quick", action="store_true",
+                    help="only the benchmark workload: skip the dense 32-variable and Zipf HUIO runs, the "
+                         "batched-vs-plain comparison and serving (several minutes together)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -541,18 +651,24 @@ def main():
         cpu = oracle_sample(inst, replicas_per_rule=args.ref_replicas, sweeps=1)
         cpu.pop("seconds", None)
 
-    small = None
-    if rank == 0 and args.small_configs:
-        small = run_small_configs(torch)
-        print(json.dumps({"small_configs": small}), file=sys.stderr, flush=True)
-
+    # ---- the other configurations (one GPU, rank 0): the dense 32-variable and
+    # Zipf HUIO runs, the batched form against the plain one, and serving; each
+    # part is written to stderr as soon as it ends, and a part that fails is
+    # recorded with its error instead of ending the benchmark
     extended = None
-    if rank == 0 and args.extended:
-        # each part is also written to stderr as soon as it ends
-        extended = {"batched_vs_plain": run_batched_vs_plain(torch)}
-        print(json.dumps({"batched_vs_plain": extended["batched_vs_plain"]}), file=sys.stderr, flush=True)
-        extended["serving"] = run_serving(torch)
-        print(json.dumps({"serving": extended["serving"]}), file=sys.stderr, flush=True)
+    if rank == 0 and world == 1 and not args.quick:
+        extended = {}
+        parts = [("small_configs", lambda: run_small_configs(torch)),
+                 ("batched_vs_plain", lambda: run_batched_vs_plain(torch, float(peaks.get("hbm_gbs", 6800.0)))),
+                 ("serving", lambda: run_serving(torch))]
+        for name, fn in parts:
+            t_part = time.perf_counter()
+            try:
+                extended[name] = fn()
+            except Exception as exc:  # recorded in the line, the benchmark goes on
+                extended[name] = {"error": f"{type(exc).__name__}: {exc}"}
+            extended[name]["wall_s"] = time.perf_counter() - t_part
+            print(json.dumps({name: extended[name]}), file=sys.stderr, flush=True)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -566,8 +682,6 @@ def main():
                 "peaks_driver": {"hbm_gbs": peaks.get("hbm_gbs"), "source": peak_kind},
                 "run_reports": reports, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": len(rules) * args.steps, "clocks": clocks}
-        if small is not None:
-            line["small_configs"] = small
         if extended is not None:
             line["extended"] = extended
         print(json.dumps(line), flush=True)

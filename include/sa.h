@@ -146,11 +146,12 @@ typedef struct {
     int32_t blocks;               /* grid size of the sweep kernel */
     int32_t n_levels;
     float kernel_ms;              /* device time of the sweep kernel (CUDA events) */
-    int32_t _reserved;
+    int32_t time_sliced;          /* 1 if the run was one time-sliced cooperative launch */
 } sa_run_report;
 
 /* Run flags */
 #define SA_FLAG_STATE_IN_GLOBAL 0x1   /* keep per-replica state in global memory even if it fits on chip */
+#define SA_FLAG_NO_TIME_SLICING 0x2   /* run more replicas than fit at once as plain waves (see sa_run) */
 
 typedef struct {
     int32_t rule;                 /* sa_rule                                              */
@@ -195,6 +196,14 @@ typedef struct {
  * (Sect. 3.1).  The kernels run the updates of variables that share no term
  * concurrently when they form a dependency level; this reproduces the
  * sequential trajectory exactly for integer models.
+ *
+ * Time slicing: when the replicas' state stays in shared memory but more
+ * replicas are requested than thread groups fit on the GPU at once, and the
+ * last of the resulting waves would be less than 95% full, the run is one
+ * cooperative launch in which the resident groups claim (replica, chunk of
+ * about S/16 sweeps) tasks one by one; consecutive chunks of a replica pass its
+ * state through a device buffer.  Results are those of the plain launch (bit
+ * for bit for integer models).  SA_FLAG_NO_TIME_SLICING disables it.
  *
  * Errors: SA_ERR_INVALID for bad parameters, SA_ERR_UNSUPPORTED for OTM on a
  * variable with exponent above 4 (Sect. 3.3.3 implements degree <= 4),
@@ -265,17 +274,26 @@ sa_status sa_batch_get_info(const sa_batch* batch, sa_batch_info* info);
 void sa_batch_destroy(sa_batch* batch);
 
 /*
- * Serving: a request loop with continuous admission.  Requests (a model and its
+ * Serving: a request loop with continuous batching.  Requests (a model and its
  * run parameters) queue in submission order; a dispatcher thread admits them,
- * skipping ahead past requests that do not fit yet, whenever one of the
- * server's streams is free and the request's device bytes (its model plus its
- * outputs, schedule and any spilled replica state) fit in budget_bytes.  Each
- * admitted request runs sa_run on its own stream, so requests admitted while
- * others run overlap on the device; finished requests release their memory and
- * stream at once.  A request's results are those of sa_run with the same model
- * and parameters, whatever else is running.
+ * skipping ahead past requests that do not fit yet, whenever a request slot is
+ * free and the request's device bytes (its model plus its outputs, schedule
+ * and any replica state too large for a shared-memory region) fit in
+ * budget_bytes.  An admitted request's replicas become units of one device
+ * work queue that a single persistent kernel drains: each of its thread groups
+ * claims the next unit and runs that replica, so requests admitted while
+ * others run share the GPU replica by replica, whatever their rule, model kind
+ * or coefficient type.  Finished requests release their memory and slot at
+ * once.  A request's results are those of sa_run with the same model and
+ * parameters (bit for bit for integer models), whatever else is running.
  *
- * sa_server_create  budget_bytes > 0; n_streams in 1..1024 (concurrent requests).
+ * While admitted requests remain, the persistent kernel occupies the GPU:
+ * calls that synchronise the whole device (cudaDeviceSynchronize, cudaFree,
+ * sa_model_destroy) from other threads wait until the server has drained.
+ *
+ * sa_server_create  budget_bytes > 0; max_running in 1..8192 (requests admitted
+ *                   at a time); threads_per_replica 0 (128), 64, 128 or 256:
+ *                   the thread-group size of the serving kernel.
  * sa_server_submit  copies params (and params->temperatures); trace,
  *                   energy_trace, report and init_states must be NULL.  The model
  *                   must stay alive until the request is finished.  A request
@@ -286,8 +304,9 @@ void sa_batch_destroy(sa_batch* batch);
  * sa_server_result  copies the results of a finished request into host buffers
  *                   (any may be NULL) and releases the ticket.
  * sa_server_get_stats  counts, device bytes in use and peak, attempts, p50/p99
- *                   latency (submission to completion) and attempts/s from the
- *                   first submission to the last completion.
+ *                   latency (submission to completion), attempts/s from the
+ *                   first submission to the last completion, finished units
+ *                   and launches of the persistent kernel.
  * sa_server_destroy cancels queued requests, waits (bounded) for running ones.
  */
 typedef struct sa_server sa_server;
@@ -298,8 +317,8 @@ typedef struct sa_server sa_server;
 #define SA_REQ_CANCELLED 4
 typedef struct {
     uint64_t budget_bytes;
-    int32_t n_streams;
-    int32_t _reserved;
+    int32_t max_running;
+    int32_t threads_per_replica;
 } sa_server_config;
 typedef struct {
     int64_t completed, failed, cancelled, queued, running;
@@ -307,6 +326,8 @@ typedef struct {
     int64_t attempts;
     double p50_latency_ms, p99_latency_ms;
     double attempts_per_s;
+    int64_t units_done;           /* finished (request, replica) units */
+    int64_t kernel_launches;      /* launches of the persistent serving kernel */
 } sa_server_stats;
 sa_status sa_server_create(sa_server** out, const sa_server_config* config);
 sa_status sa_server_submit(sa_server* server, const sa_model* model, const sa_run_params* params, uint64_t* ticket);

@@ -24,6 +24,7 @@ STATUS_NAMES = ["SA_OK", "SA_ERR_INVALID", "SA_ERR_OVERFLOW", "SA_ERR_UNSUPPORTE
 COEF = {"i32": 0, "i64": 1, "f32": 2, "f64": 3}
 RULES = {"metropolis": 0, "heat_bath": 1, "opt_metropolis": 2}
 SA_FLAG_STATE_IN_GLOBAL = 0x1
+SA_FLAG_NO_TIME_SLICING = 0x2
 
 
 class SAError(RuntimeError):
@@ -42,7 +43,7 @@ class sa_model_info(C.Structure):
 class sa_run_report(C.Structure):
     _fields_ = [("max_refresh_drift", C.c_double), ("replicas_per_block", C.c_int32),
                 ("threads_per_replica", C.c_int32), ("state_in_global", C.c_int32), ("shared_bytes", C.c_int32),
-                ("blocks", C.c_int32), ("n_levels", C.c_int32), ("kernel_ms", C.c_float), ("_reserved", C.c_int32)]
+                ("blocks", C.c_int32), ("n_levels", C.c_int32), ("kernel_ms", C.c_float), ("time_sliced", C.c_int32)]
 
 
 class sa_batch_info(C.Structure):
@@ -53,14 +54,14 @@ class sa_batch_info(C.Structure):
 
 
 class sa_server_config(C.Structure):
-    _fields_ = [("budget_bytes", C.c_uint64), ("n_streams", C.c_int32), ("_reserved", C.c_int32)]
+    _fields_ = [("budget_bytes", C.c_uint64), ("max_running", C.c_int32), ("threads_per_replica", C.c_int32)]
 
 
 class sa_server_stats(C.Structure):
     _fields_ = [("completed", C.c_int64), ("failed", C.c_int64), ("cancelled", C.c_int64), ("queued", C.c_int64),
                 ("running", C.c_int64), ("device_bytes_in_use", C.c_int64), ("device_bytes_peak", C.c_int64),
                 ("attempts", C.c_int64), ("p50_latency_ms", C.c_double), ("p99_latency_ms", C.c_double),
-                ("attempts_per_s", C.c_double)]
+                ("attempts_per_s", C.c_double), ("units_done", C.c_int64), ("kernel_launches", C.c_int64)]
 
 
 class sa_peaks(C.Structure):
@@ -311,8 +312,8 @@ def sa_batch_destroy(b):
         load().sa_batch_destroy(b)
 
 
-def sa_server_create(budget_bytes, n_streams=16):
-    cfg = sa_server_config(int(budget_bytes), int(n_streams), 0)
+def sa_server_create(budget_bytes, max_running=1024, threads_per_replica=0):
+    cfg = sa_server_config(int(budget_bytes), int(max_running), int(threads_per_replica))
     out = C.c_void_p()
     _check(load().sa_server_create(C.byref(out), C.byref(cfg)))
     return out.value

@@ -844,13 +844,51 @@ sa_status sa_run(const sa_model* M, const sa_run_params* p, int32_t* out_states,
     a.gstate = gstate;
     sa::plan_apply(plan, a);
 
+    // ---- time slicing: when the replicas need more than one wave of resident
+    // thread groups and the last wave would leave slots idle, one cooperative
+    // launch lets the resident groups claim (replica, chunk of sweeps) tasks
+    // (sa::slice_chunk_sweeps); results are those of the plain launch
+    int grid_sliced = 0;
+    unsigned int* d_status = nullptr;
+    if (!in_global && !(p->flags & SA_FLAG_NO_TIME_SLICING) && shared + 64 <= (size_t)sa::sweep_max_shared_optin()) {
+        int bps = 0;
+        if (sa::launch_sweep_sliced(a, M->zbytes, p->rule, 0, rpc * tpr, shared, stream, &bps) == 0 && bps > 0) {
+            const int64_t slots = (int64_t)dev_sms * bps * rpc;
+            const int64_t waves = (R + slots - 1) / slots;
+            if (R > slots && (double)R < 0.95 * (double)(waves * slots)) grid_sliced = dev_sms * bps;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    if (grid_sliced > 0) {
+        a.handoff_bytes = (int64_t)align_up((size_t)plan.off_ctl + (size_t)tpr * 24, 16);
+        uint8_t* d_hand = nullptr;
+        if ((e = tmp.alloc((void**)&d_hand, (size_t)R * (size_t)a.handoff_bytes + (size_t)R * 4 + 16)) !=
+            cudaSuccess)
+            return cuda_fail(e, "alloc handoff");
+        a.handoff = d_hand;
+        a.handoff_flag = reinterpret_cast<unsigned int*>(d_hand + (size_t)R * (size_t)a.handoff_bytes);
+        d_status = a.handoff_flag + R;
+        a.status = d_status;
+        cudaMemsetAsync(a.handoff_flag, 0, (size_t)R * 4 + 16, st);
+    }
+
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (p->report) {
         cudaEventCreate(&ev0);
         cudaEventCreate(&ev1);
         cudaEventRecord(ev0, st);
     }
-    int le = sa::launch_sweep(a, M->zbytes, p->rule, !in_global, blocks, rpc * tpr, shared, stream);
+    int le = 1;
+    if (grid_sliced > 0) {
+        le = sa::launch_sweep_sliced(a, M->zbytes, p->rule, grid_sliced, rpc * tpr, shared, stream, nullptr);
+        if (le != 0) {
+            cudaGetLastError();   // the cooperative launch was refused: run the plain launch instead
+            grid_sliced = 0;
+            d_status = nullptr;
+        }
+    }
+    if (grid_sliced == 0) le = sa::launch_sweep(a, M->zbytes, p->rule, !in_global, blocks, rpc * tpr, shared, stream);
     if (le != 0) return cuda_fail((cudaError_t)le, "sweep launch");
     if (p->report) cudaEventRecord(ev1, st);
 
@@ -863,8 +901,13 @@ sa_status sa_run(const sa_model* M, const sa_run_params* p, int32_t* out_states,
     unsigned int drift_h = 0;
     if (d_drift && (e = cudaMemcpyAsync(&drift_h, d_drift, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_fail(e, "copy drift");
+    unsigned int status_h = 0;
+    if (d_status && sync_needed &&
+        (e = cudaMemcpyAsync(&status_h, d_status, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(e, "copy status");
     if (sync_needed) {
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "sa_run");
+        if (status_h) return fail(SA_ERR_TIMEOUT, "a state handoff between thread groups timed out");
     }
     if (p->report) {
         sa_run_report* rp = p->report;
@@ -879,9 +922,10 @@ sa_status sa_run(const sa_model* M, const sa_run_params* p, int32_t* out_states,
         rp->threads_per_replica = tpr;
         rp->state_in_global = in_global ? 1 : 0;
         rp->shared_bytes = (int32_t)shared;
-        rp->blocks = blocks;
+        rp->blocks = grid_sliced > 0 ? grid_sliced : blocks;
         rp->n_levels = M->n_levels;
         rp->kernel_ms = ms;
+        rp->time_sliced = grid_sliced > 0 ? 1 : 0;
     }
     return SA_OK;
 }

@@ -22,6 +22,21 @@ int launch_sweep(const SweepArgs& a, int zbytes, int rule, bool smem, int blocks
     return launch_sweep_huio_i64(a, zbytes, rule, smem, blocks, threads, shared_bytes, stream);
 }
 
+int launch_sliced_quio_i64(const SweepArgs&, int, int, int, int, size_t, void*, int*);
+int launch_sliced_quio_f32(const SweepArgs&, int, int, int, int, size_t, void*, int*);
+int launch_sliced_huio_i64(const SweepArgs&, int, int, int, int, size_t, void*, int*);
+int launch_sliced_huio_f32(const SweepArgs&, int, int, int, int, size_t, void*, int*);
+
+int launch_sweep_sliced(const SweepArgs& a, int zbytes, int rule, int grid, int threads, size_t shared_bytes,
+                        void* stream, int* bps) {
+    if (a.m.kind == KIND_QUIO) {
+        if (a.m.is_float) return launch_sliced_quio_f32(a, zbytes, rule, grid, threads, shared_bytes, stream, bps);
+        return launch_sliced_quio_i64(a, zbytes, rule, grid, threads, shared_bytes, stream, bps);
+    }
+    if (a.m.is_float) return launch_sliced_huio_f32(a, zbytes, rule, grid, threads, shared_bytes, stream, bps);
+    return launch_sliced_huio_i64(a, zbytes, rule, grid, threads, shared_bytes, stream, bps);
+}
+
 int launch_batch_quio_i64(const BatchArgs&, int, int, bool, int, int, size_t, void*, bool);
 int launch_batch_quio_f32(const BatchArgs&, int, int, bool, int, int, size_t, void*, bool);
 int launch_batch_huio_i64(const BatchArgs&, int, int, bool, int, int, size_t, void*, bool);

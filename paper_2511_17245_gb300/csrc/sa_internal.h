@@ -109,6 +109,14 @@ struct SweepArgs {
     int32_t tpr;                // threads per replica (multiple of 32)
     int32_t heavy_links;        // link_len above which updates are cooperative
     int32_t list_cap;           // capacity of the cooperative update list
+    // time-sliced runs (sweep_sliced_kernel): per-replica regions through which
+    // a replica's state passes from one chunk of sweeps to the next, the number
+    // of finished chunks per replica, the task counter and an error word
+    uint8_t* handoff;
+    unsigned int* handoff_flag; // [R]: chunks of the replica finished (and saved)
+    int64_t handoff_bytes;      // bytes of one region: off_ctl + 24 per thread, rounded to 16
+    unsigned int* status;       // [0] bit 0: a handoff wait gave up (that replica's outputs are not
+                                // written); [1]: task counter
 };
 
 // One unit of batched work: one replica of one instance.
@@ -127,6 +135,51 @@ struct BatchArgs {
     int32_t rpc, tpr;
     uint8_t* gstate;            // per-group regions when the state is not on chip
 };
+
+// ------------------------------------------------------------------ serving
+// One admitted request of the server: the kernel arguments of its run (the
+// fields of SweepArgs, with the layout for the serving kernel's group size)
+// and which compiled variant runs it.  Written by the host into host-mapped
+// memory before the request's units are published.
+struct ServeReq {
+    SweepArgs args;
+    int32_t variant;            // serve_variant(...)
+    int32_t n_units;            // replicas
+};
+
+// A unit of serving work: one replica of one admitted request.
+struct ServeUnit {
+    int32_t req;                // request slot
+    int32_t replica;
+};
+
+// Host-mapped control words of the serving queue.
+struct ServeCtl {
+    volatile uint32_t tail;     // units published so far (host writes)
+    volatile uint32_t stop;     // nonzero: groups leave once the queue is empty
+};
+
+// Arguments of the persistent serving kernel.
+struct ServeArgs {
+    const ServeReq* reqs;       // [max_reqs], host-mapped
+    const ServeUnit* units;     // ring of `cap` units, host-mapped
+    const ServeCtl* ctl;        // host-mapped
+    unsigned int* head;         // device: next unit to claim
+    unsigned int* req_units_done;   // device: [max_reqs] finished units per request slot
+    unsigned int* req_done;     // host-mapped: [max_reqs] set to 1 when a request's last unit finished
+    uint32_t cap;               // ring capacity (a power of two)
+    int32_t tpr, rpc;
+    int32_t _pad0;
+    int64_t slot_bytes;         // shared-memory state region of one thread group
+    uint32_t idle_polls;        // empty-queue polls (about 2 us each) before a group leaves
+    uint32_t _pad1;
+};
+
+// Variant index of a request for the serving kernel: rule, model kind,
+// coefficient class and 2- or 4-byte state offsets.
+inline int serve_variant(int rule, int kind, int is_float, int zbytes) {
+    return rule + 3 * (kind + 2 * (is_float + 2 * (zbytes > 2 ? 1 : 0)));
+}
 
 // Arguments of the energy kernel.
 struct EnergyArgs {
@@ -269,64 +322,25 @@ inline const char* plan_run_shape(const PlanModel& m, int32_t R, int32_t tpr_req
 // ------------------------------------------------------------------ time-sliced runs
 // When R replicas exceed the P thread groups that can be resident at once, a
 // plain launch runs ceil(R / P) waves and the last one leaves slots idle.  A
-// time-sliced launch instead gives every slot p an equal share of the
-// flattened sequence u = r S + s of (replica, sweep) pairs: a contiguous range
-// of Q_p = floor(R S / P) or one more pairs, Q_p >= S when R >= P.  A replica
-// cut by a range boundary has its first sweeps (the head) at the end of slot
-// p's range and its last sweeps (the tail) at the start of slot p + 1's range;
-// each slot runs its head piece first, then its whole replicas, then its tail
-// piece.  The head on slot p ends after s_b sweeps of that slot and the tail on
-// slot p + 1 starts after Q_{p+1} - (S - s_b) >= s_b sweeps of its slot, so the
-// handoff of the replica's state never waits on work queued behind it.
-struct SlicePiece {
-    int32_t r;          // replica
-    int32_t s0, s1;     // sweeps [s0, s1)
-};
-struct SlicePlan {
-    int32_t n;          // pieces (0..3 groups: head, whole replicas as a range, tail)
-    SlicePiece head;    // s0 == 0, s1 < S (valid if has_head)
-    int32_t has_head;
-    int32_t whole_r0, whole_r1;   // whole replicas [whole_r0, whole_r1)
-    SlicePiece tail;    // s0 > 0, s1 == S (valid if has_tail)
-    int32_t has_tail;
-};
+// time-sliced launch instead cuts every replica's S sweeps into C chunks of K
+// sweeps and lets the resident groups claim (replica, chunk) tasks from one
+// counter in chunk-major order: task q is chunk q / R of replica q % R.  A
+// chunk after the first waits for its replica's previous chunk, restores the
+// state that chunk saved and saves its own for the next.  Every task's
+// predecessor was claimed earlier by a resident group, so the chain of waits
+// always ends at a running task; and with R >= P a predecessor was claimed
+// about R tasks earlier, so it has usually finished.  Claiming tasks one by one
+// balances the groups by the actual cost of the sweeps (which varies along the
+// schedule), the last round of tasks being one chunk long.
+constexpr int kSliceChunks = 16;
 
-// Pieces of slot p (0 <= p < P) for R replicas of S sweeps over P slots.
+// Sweeps per chunk of a time-sliced run of S sweeps (at most kSliceChunks chunks).
 inline
 #ifdef __CUDACC__
 __host__ __device__
 #endif
-SlicePlan slice_plan(int64_t p, int32_t R, int32_t S, int64_t P) {
-    SlicePlan sp{};
-    sp.whole_r0 = sp.whole_r1 = 0;
-    const int64_t total = (int64_t)R * S;
-    const int64_t base = total / P, rem = total % P;
-    const int64_t u0 = p * base + (p < rem ? p : rem);
-    const int64_t u1 = u0 + base + (p < rem ? 1 : 0);
-    if (u0 >= u1) return sp;
-    int32_t r_first = (int32_t)(u0 / S), s_first = (int32_t)(u0 % S);
-    const int32_t r_last = (int32_t)((u1 - 1) / S), s_end = (int32_t)((u1 - 1) % S) + 1;
-    if (s_first > 0) {
-        // the range starts inside replica r_first: its tail (its head is on slot p - 1)
-        sp.has_tail = 1;
-        sp.tail = SlicePiece{r_first, s_first, r_first == r_last ? s_end : S};
-        ++r_first;
-        s_first = 0;
-    }
-    if (r_first <= r_last) {
-        if (s_end < S) {
-            // the range ends inside replica r_last: its head (its tail is on slot p + 1)
-            sp.has_head = 1;
-            sp.head = SlicePiece{r_last, 0, s_end};
-            sp.whole_r0 = r_first;
-            sp.whole_r1 = r_last;
-        } else {
-            sp.whole_r0 = r_first;
-            sp.whole_r1 = r_last + 1;
-        }
-    }
-    sp.n = sp.has_head + sp.has_tail + (sp.whole_r1 - sp.whole_r0);
-    return sp;
+int32_t slice_chunk_sweeps(int32_t S) {
+    return (S + kSliceChunks - 1) / kSliceChunks;
 }
 
 // Per-sweep table read by the kernel: tab[s] = fp32(1 / T_s) with the geometric
@@ -380,9 +394,18 @@ inline void plan_apply(const RunPlan& p, SweepArgs& a) {
 int launch_sweep(const SweepArgs& a, int zbytes, int rule, bool smem, int blocks, int threads,
                  size_t shared_bytes, void* stream);
 int launch_energy(const EnergyArgs& a, void* stream);
+// Time-sliced cooperative launch of `grid` blocks (state in shared memory);
+// with grid = 0 it only reports the resident blocks per SM in *blocks_per_sm.
+int launch_sweep_sliced(const SweepArgs& a, int zbytes, int rule, int grid, int threads, size_t shared_bytes,
+                        void* stream, int* blocks_per_sm);
 // Persistent batched kernel; set_attr = false during stream capture.
 int launch_batch(const BatchArgs& b, int is_float, int kind, int zbytes, int rule, bool smem, int blocks,
                  int threads, size_t shared_bytes, void* stream, bool set_attr);
 int sweep_max_shared_optin();
+// Persistent serving kernel (blocks of rpc * tpr threads; grid = 0 only sets
+// the shared-memory attribute); returns a cudaError_t as int.
+int launch_serve(const ServeArgs& s, int grid, size_t shared_bytes, void* stream);
+// Static shared memory of the serving kernel (per block).
+size_t serve_static_shared();
 
 }  // namespace sa

@@ -630,8 +630,13 @@ __device__ __forceinline__ float quio_w(float dz, float A, float B, float C) {
     return ex2_ftz(fmaf(fmaf(A, dz, B), dz, C));
 }
 
+// The window only has to contain every value within the cut, and every bound
+// below carries a margin of at least one value, so its arithmetic uses the
+// fast approximate divide, reciprocal square root and logarithm (relative
+// errors of a few ulp); the weights themselves are computed as elsewhere.
+// `temp` is T = 1 / beta.
 __device__ __forceinline__ long long heat_bath_quio_f32_small(float f, float d, long long z, long long lo,
-                                                              uint32_t width, uint32_t xu, float beta) {
+                                                              uint32_t width, uint32_t xu, float beta, float temp) {
     const int n = (int)width + 1;
     const float zf = __int2float_rn((int)z);
     const float dz0 = __int2float_rn((int)(lo - z));
@@ -639,22 +644,23 @@ __device__ __forceinline__ long long heat_bath_quio_f32_small(float f, float d, 
     const float dzn = dz0 + (float)width;
     const float e0 = dz0 * fmaf(d, dz0, c1), en = dzn * fmaf(d, dzn, c1);
     float mn = fminf(0.f, fminf(e0, en));
-    const float C = hb_cut(width) / beta;
+    const float C = (20.f + __logf((float)width + 1.f)) * temp;   // hb_cut(width) / beta
     float wlo = dz0, whi = dzn;
     if (d > 0.f) {
-        const float vq = -c1 / (2.f * d);
+        const float vq = __fdividef(-c1, 2.f * d);
         if (vq > dz0 && vq < dzn) {
             const float q = floorf(vq), q1 = q + 1.f;
             mn = fminf(mn, fminf(q * fmaf(d, q, c1), q1 * fmaf(d, q1, c1)));
-            const float h = sqrtf(C / d + 0.25f) + 1.f;
+            const float h2 = __fdividef(C, d) + 0.25f;
+            const float h = h2 * rsqrtf(h2) + 1.f;                  // sqrt(C / d + 1/4) + 1
             wlo = fmaxf(dz0, floorf(vq - h));
             whi = fminf(dzn, ceilf(vq + h));
         } else if (vq <= dz0) {      // increasing over the range: minimum at dz0
             const float slope = fmaf(d, fmaf(2.f, dz0, 1.f), c1);   // dE(dz0 + 1) - dE(dz0) > 0
-            whi = fminf(dzn, dz0 + ceilf(C / slope) + 1.f);
+            whi = fminf(dzn, dz0 + ceilf(__fdividef(C, slope)) + 1.f);
         } else {                      // decreasing: minimum at dzn
             const float slope = -fmaf(d, fmaf(2.f, dzn, -1.f), c1); // dE(dzn - 1) - dE(dzn) > 0
-            wlo = fmaxf(dz0, dzn - ceilf(C / slope) - 1.f);
+            wlo = fmaxf(dz0, dzn - ceilf(__fdividef(C, slope)) - 1.f);
         }
         if (!(wlo <= whi)) { wlo = dz0; whi = dzn; }   // non-finite slope etc.: whole range
     }
@@ -664,52 +670,48 @@ __device__ __forceinline__ long long heat_bath_quio_f32_small(float f, float d, 
     const int base = kb0 * 16;
     const int nrb = kb1 - kb0 + 1;
     const float dzb0 = dz0 + (float)base;
+    // block sums in registers (the loops are unrolled, so bs[] is indexed by
+    // constants); both loops stop after the window's nrb blocks
     float bs[16];
     float tot = 0.f;
 #pragma unroll
     for (int b = 0; b < 16; ++b) {
+        if (b >= nrb) break;
         float acc = 0.f;
-        if (b < nrb) {
-            const float a0 = dzb0 + (float)(b * 16);
-            if (base + b * 16 + 15 < n) {
-                float w[16];
+        const float a0 = dzb0 + (float)(b * 16);
+        if (base + b * 16 + 15 < n) {
+            float w[16];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) w[j] = quio_w(a0 + (float)j, hA, hB, mb);
+            for (int j = 0; j < 16; ++j) w[j] = quio_w(a0 + (float)j, hA, hB, mb);
 #pragma unroll
-                for (int h = 8; h >= 1; h >>= 1)
+            for (int h = 8; h >= 1; h >>= 1)
 #pragma unroll
-                    for (int j = 0; j < h; ++j) w[j] += w[j + h];
-                acc = w[0];
-            } else {
-                const int cnt = n - (base + b * 16);
-                for (int j = 0; j < cnt; ++j) acc += quio_w(a0 + (float)j, hA, hB, mb);
-            }
+                for (int j = 0; j < h; ++j) w[j] += w[j + h];
+            acc = w[0];
+        } else {
+            const int cnt = n - (base + b * 16);
+            for (int j = 0; j < cnt; ++j) acc += quio_w(a0 + (float)j, hA, hB, mb);
         }
         bs[b] = acc;
         tot += acc;
     }
     const float thr = unit_open_left(xu) * tot;
-    float run = 0.f;
+    float run = 0.f, before_last = 0.f;
     int sel = -1;
 #pragma unroll
     for (int b = 0; b < 16; ++b) {
-        if (sel < 0 && b < nrb) {
-            const float nxt = run + bs[b];
-            if (nxt >= thr) sel = b;
-            else run = nxt;
+        if (b >= nrb) break;
+        const float nxt = run + bs[b];
+        if (nxt >= thr) {
+            sel = b;
+            break;
         }
+        before_last = run;
+        run = nxt;
     }
     if (sel < 0) {  // rounding left the threshold above the window: take its last block
-        float before = 0.f, acc = 0.f;
-#pragma unroll
-        for (int b = 0; b < 16; ++b) {
-            if (b < nrb) {
-                sel = b;
-                before = acc;
-                acc += bs[b];
-            }
-        }
-        run = before;
+        sel = nrb - 1;
+        run = before_last;
     }
     const int first = base + sel * 16;
     const int last = min(first + 15, n - 1);
@@ -1009,15 +1011,23 @@ __device__ T group_sum(T v, T* red, int t, int tpr, int bar_id) {
 }
 
 // ------------------------------------------------------------------ one replica
-// The whole SA run of replica r (Sect. 3.1) by the `tpr` threads of one group;
-// `base` is the group's state region (shared or global memory).
+// Sweeps [s0, s1) of the SA run of replica r (Sect. 3.1) by the `tpr` threads
+// of one group; `base` is the group's state region (shared or global memory).
+// A run that starts at s0 = 0 draws (or takes) the initial state and builds
+// the caches; otherwise it restores the state and the per-thread accumulators
+// that the run of sweeps [0, s0) saved at `restore`.  A run that ends at
+// s1 = S writes the outputs; otherwise it saves its state at `save` (layout:
+// bytes [0, off_ctl) of the state region, then per thread the energy
+// accumulator, the change count and the refresh drift, 24 bytes each).
 template <class F, class Z, int RULE, int KIND>
 __device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot, const int t, const int r,
-                                             uint8_t* base) {
+                                             uint8_t* base, const int s0 = 0, int s1 = -1,
+                                             const uint8_t* restore = nullptr, uint8_t* save = nullptr) {
     using Acc = typename Num<F>::Acc;
     const DevModel& m = a.m;
     const int bar_id = 1 + slot;
     const int tpr = a.tpr;
+    if (s1 < 0) s1 = a.S;
     Z* zs = reinterpret_cast<Z*>(base + a.off_z);
     F* cache = reinterpret_cast<F*>(base + a.off_cache);
     int* ctl = reinterpret_cast<int*>(base + a.off_ctl);      // [3] list counters, [3] flattened length
@@ -1026,52 +1036,66 @@ __device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot,
     int* list = reinterpret_cast<int*>(base + a.off_list);
     Acc* red = reinterpret_cast<Acc*>(base + a.off_red);
 
-    // ---- random initial state (Sect. 3.1), or the caller's
-    for (int k = t; k < m.n; k += tpr) {
-        const VarMeta mt = m.meta[k];
-        uint32_t off;
-        if (a.init_states) {
-            off = (uint32_t)((long long)a.init_states[(size_t)r * m.n + k] - (long long)mt.lo);
-        } else {
-            const Words4 x = philox4x32_10((uint32_t)k, 0xFFFFFFFFu, (uint32_t)r, a.inst, a.key0, a.key1);
-            off = pick_below(x.x0, mt.width + 1u);
-        }
-        zs[k] = (Z)off;
-    }
     if (t == 0) { ctl[0] = 0; ctl[1] = 0; ctl[2] = 0; }
     // level boundaries, staged on chip when the table is small
     int* lvl_s = a.off_lvl >= 0 ? reinterpret_cast<int*>(base + a.off_lvl) : nullptr;
     if (lvl_s)
         for (int L = t; L <= m.n_levels; L += tpr) lvl_s[L] = __ldg(m.lvl_ptr + L);
-    named_bar(bar_id, tpr);
 
     float drift = 0.f;
-    Acc e1 = 0, e2 = 0;
-    if constexpr (KIND == KIND_QUIO) quio_recompute<F, Z>(m, zs, cache, t, tpr, false, drift, e1, e2);
-    else huio_recompute<F, Z>(m, zs, cache, t, tpr, false, drift, e1, e2);
-    // per-thread energy accumulator: this thread's share of E(z_init)
     Acc eacc;
-    if constexpr (KIND == KIND_QUIO) {
-        // pair share is counted twice over the replica; halve after the sum
-        Acc pair2 = group_sum<Acc>(e2, red, t, tpr, bar_id);
-        eacc = e1 + (t == 0 ? pair2 / 2 : Acc(0));
+    unsigned long long changes = 0;
+    if (restore == nullptr) {
+        // ---- random initial state (Sect. 3.1), or the caller's
+        for (int k = t; k < m.n; k += tpr) {
+            const VarMeta mt = m.meta[k];
+            uint32_t off;
+            if (a.init_states) {
+                off = (uint32_t)((long long)a.init_states[(size_t)r * m.n + k] - (long long)mt.lo);
+            } else {
+                const Words4 x = philox4x32_10((uint32_t)k, 0xFFFFFFFFu, (uint32_t)r, a.inst, a.key0, a.key1);
+                off = pick_below(x.x0, mt.width + 1u);
+            }
+            zs[k] = (Z)off;
+        }
+        named_bar(bar_id, tpr);
+        Acc e1 = 0, e2 = 0;
+        if constexpr (KIND == KIND_QUIO) quio_recompute<F, Z>(m, zs, cache, t, tpr, false, drift, e1, e2);
+        else huio_recompute<F, Z>(m, zs, cache, t, tpr, false, drift, e1, e2);
+        // per-thread energy accumulator: this thread's share of E(z_init)
+        if constexpr (KIND == KIND_QUIO) {
+            // pair share is counted twice over the replica; halve after the sum
+            Acc pair2 = group_sum<Acc>(e2, red, t, tpr, bar_id);
+            eacc = e1 + (t == 0 ? pair2 / 2 : Acc(0));
+        } else {
+            eacc = e1 + e2;
+            named_bar(bar_id, tpr);
+        }
+        if (t == 0) {
+            if constexpr (Num<F>::is_float) eacc += m.const_d;
+            else eacc += m.const_i;
+        }
     } else {
-        eacc = e1 + e2;
+        // ---- state of sweeps [0, s0), saved by another group
+        const int nq = a.off_ctl / 16;
+        const uint4* src = reinterpret_cast<const uint4*>(restore);
+        uint4* dst = reinterpret_cast<uint4*>(base);
+        for (int q = t; q < nq; q += tpr) dst[q] = __ldcg(src + q);
+        const uint8_t* acc = restore + a.off_ctl + (size_t)t * 24;
+        const unsigned long long e_bits = __ldcg(reinterpret_cast<const unsigned long long*>(acc));
+        eacc = *reinterpret_cast<const Acc*>(&e_bits);
+        changes = __ldcg(reinterpret_cast<const unsigned long long*>(acc + 8));
+        drift = __ldcg(reinterpret_cast<const float*>(acc + 16));
         named_bar(bar_id, tpr);
     }
-    if (t == 0) {
-        if constexpr (Num<F>::is_float) eacc += m.const_d;
-        else eacc += m.const_i;
-    }
 
-    unsigned long long changes = 0;
     float dacc = 0.f;  // float models: energy changes since the last fold into eacc
     int gl3 = 0;  // level counter mod 3: which cooperative-list counter is live
 
     // Decision for one record (reads replica state only).  With `wmode` the 32
     // lanes of a warp call it together for the same record (heat bath only).
-    auto decide = [&](const LevelRec& rc, int s, float beta, float ratio, long long& z, long long& v, F& de,
-                      bool wmode) {
+    auto decide = [&](const LevelRec& rc, int s, float beta, float temp, float ratio, long long& z, long long& v,
+                      F& de, bool wmode) {
         const int k = rc.k;
         const long long lo = rc.lo;
         const long long zo = (long long)zs[k];
@@ -1099,7 +1123,7 @@ __device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot,
                 bool done = false;
                 if constexpr (Num<F>::is_float && KIND == KIND_QUIO) {
                     if (rc.width < 256u && lo > -(1 << 22) && hi < (1 << 22)) {
-                        v = heat_bath_quio_f32_small((float)vv.f, (float)vv.d, z, lo, rc.width, x.x0, beta);
+                        v = heat_bath_quio_f32_small((float)vv.f, (float)vv.d, z, lo, rc.width, x.x0, beta, temp);
                         done = true;
                     }
                 }
@@ -1171,8 +1195,9 @@ __device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot,
     };
     prefetch_level(0);
 
-    for (int s = 0; s < a.S; ++s) {
+    for (int s = s0; s < s1; ++s) {
         const float beta = __ldg(a.beta + s);
+        const float temp = 1.f / beta;
         const float ratio = __ldg(a.ratio + s);
         for (int L = 0; L < m.n_levels; ++L) {
             int* cnt_now = ctl + gl3;
@@ -1202,7 +1227,7 @@ __device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot,
                     const LevelRec rc = load_rec(i);
                     long long zz, vv2;
                     F d2;
-                    decide(rc, s, beta, ratio, zz, vv2, d2, wmode);
+                    decide(rc, s, beta, temp, ratio, zz, vv2, d2, wmode);
                     if (!wmode || lane == 0) {
                         apply(rc, s, zz, vv2, d2, cnt_now, coop);
                         rb = rc.link_begin;
@@ -1327,6 +1352,20 @@ __device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot,
         }
     }
 
+    if (save != nullptr) {
+        // ---- hand the state of sweeps [0, s1) to the group that runs the rest
+        named_bar(bar_id, tpr);
+        const int nq = a.off_ctl / 16;
+        const uint4* src = reinterpret_cast<const uint4*>(base);
+        uint4* dst = reinterpret_cast<uint4*>(save);
+        for (int q = t; q < nq; q += tpr) dst[q] = src[q];
+        uint8_t* acc = save + a.off_ctl + (size_t)t * 24;
+        *reinterpret_cast<Acc*>(acc) = eacc;
+        *reinterpret_cast<unsigned long long*>(acc + 8) = changes;
+        *reinterpret_cast<float*>(acc + 16) = drift;
+        return;
+    }
+
     // ---- outputs
     const Acc etot = group_sum<Acc>(eacc, red, t, tpr, bar_id);
     const unsigned long long ctot = group_sum<unsigned long long>(changes, reinterpret_cast<unsigned long long*>(red), t, tpr, bar_id);
@@ -1357,6 +1396,81 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepArgs a) {
     if (slot >= a.rpc || r >= a.R) return;
     uint8_t* base = SMEM ? (smem_raw + (size_t)slot * (size_t)a.rep_bytes) : (a.gstate + (size_t)r * (size_t)a.rep_bytes);
     replica_body<F, Z, RULE, KIND>(a, slot, t, r, base);
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned int* p, unsigned int v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Upper bound on the polls of a handoff flag (each followed by a ~256 ns
+// sleep).  The awaited chunk waits only on chunks claimed before it, so the
+// bound only matters if the launch was not co-resident.
+constexpr unsigned long long kHandoffSpinLimit = 1ull << 32;
+
+// Time-sliced run of R replicas on the thread groups of a cooperative grid
+// (every block resident at once): the groups claim (replica, chunk) tasks in
+// chunk-major order (see slice_chunk_sweeps); a chunk after the first waits
+// (bounded) until its replica's previous chunk has saved its state, restores
+// it, runs its sweeps and saves the state for the next chunk.  Per-replica
+// results equal those of sweep_kernel: every chunk draws the same Philox
+// counters and the saved state includes the per-thread accumulators.
+template <class F, class Z, int RULE, int KIND>
+__global__ void __launch_bounds__(512, 1) sweep_sliced_kernel(const SweepArgs a) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    __shared__ int task_s[16][2];
+    const int slot = threadIdx.x / a.tpr;
+    const int t = threadIdx.x - slot * a.tpr;
+    if (slot >= a.rpc) return;
+    const int bar_id = 1 + slot;
+    uint8_t* base = smem_raw + (size_t)slot * (size_t)a.rep_bytes;
+    const int32_t K = slice_chunk_sweeps(a.S);
+    const int32_t C = (a.S + K - 1) / K;
+    const unsigned int n_tasks = (unsigned int)a.R * (unsigned int)C;
+    for (;;) {
+        named_bar(bar_id, a.tpr);   // the previous task is done with the state region and task_s
+        if (t == 0) {
+            const unsigned int q = atomicAdd(a.status + 1, 1u);
+            int ok = 1;
+            if (q < n_tasks) {
+                const int32_t j = (int32_t)(q / (unsigned int)a.R);
+                const int32_t r = (int32_t)(q % (unsigned int)a.R);
+                if (j > 0) {
+                    unsigned int seen = 0;
+                    for (unsigned long long it = 0; it < kHandoffSpinLimit; ++it) {
+                        seen = ld_acquire_gpu(a.handoff_flag + r);
+                        if (seen >= (unsigned int)j) break;
+                        __nanosleep(256);
+                    }
+                    if (seen < (unsigned int)j) {
+                        atomicOr(a.status, 1u);
+                        ok = 0;
+                    }
+                }
+            }
+            task_s[slot][0] = q < n_tasks ? (int)q : -1;
+            task_s[slot][1] = ok;
+        }
+        named_bar(bar_id, a.tpr);
+        const int q = task_s[slot][0];
+        if (q < 0) break;
+        if (!task_s[slot][1]) continue;   // the wait gave up: skip this chunk (status set)
+        const int32_t j = q / a.R, r = q % a.R;
+        const int32_t s0 = j * K, s1 = min(a.S, s0 + K);
+        uint8_t* region = a.handoff + (size_t)r * (size_t)a.handoff_bytes;
+        if (j > 0) __threadfence();
+        replica_body<F, Z, RULE, KIND>(a, slot, t, r, base, s0, s1, j > 0 ? region : nullptr,
+                                       s1 < a.S ? region : nullptr);
+        if (s1 < a.S) {
+            __threadfence();
+            named_bar(bar_id, a.tpr);
+            if (t == 0) st_release_gpu(a.handoff_flag + r, (unsigned int)(j + 1));
+        }
+    }
 }
 
 // Many instances in one persistent launch: every thread group repeatedly claims

@@ -10,4 +10,8 @@ int launch_batch_huio_i64(const BatchArgs& b, int zbytes, int rule, bool smem, i
                              size_t sh, void* stream, bool set_attr) {
     return launch_batch_family<long long, KIND_HUIO>(b, zbytes, rule, smem, blocks, threads, sh, (cudaStream_t)stream, set_attr);
 }
+int launch_sliced_huio_i64(const SweepArgs& a, int zbytes, int rule, int grid, int threads, size_t sh, void* stream,
+                        int* bps) {
+    return launch_sliced_family<long long, KIND_HUIO>(a, zbytes, rule, grid, threads, sh, (cudaStream_t)stream, bps);
+}
 }  // namespace sa

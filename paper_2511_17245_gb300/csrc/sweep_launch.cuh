@@ -39,6 +39,40 @@ static int launch_family(const SweepArgs& a, int zbytes, int rule, bool smem, in
     return launch_rule<F, uint32_t, KIND, false>(a, rule, blocks, threads, sh, st);
 }
 
+template <class F, class Z, int RULE, int KIND>
+static int launch_sliced_one(const SweepArgs& a, int grid, int threads, size_t shared_bytes, cudaStream_t st,
+                             int* blocks_per_sm) {
+    auto kern = dev::sweep_sliced_kernel<F, Z, RULE, KIND>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shared_bytes);
+    if (e != cudaSuccess) return (int)e;
+    if (grid == 0) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, threads, shared_bytes);
+        return (int)e;
+    }
+    SweepArgs args = a;
+    void* params[] = {&args};
+    e = cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(threads), params, shared_bytes, st);
+    return (int)e;
+}
+
+template <class F, class Z, int KIND>
+static int launch_sliced_rule(const SweepArgs& a, int rule, int grid, int threads, size_t sh, cudaStream_t st,
+                              int* bps) {
+    switch (rule) {
+    case RULE_METROPOLIS: return launch_sliced_one<F, Z, RULE_METROPOLIS, KIND>(a, grid, threads, sh, st, bps);
+    case RULE_HEAT_BATH: return launch_sliced_one<F, Z, RULE_HEAT_BATH, KIND>(a, grid, threads, sh, st, bps);
+    default: return launch_sliced_one<F, Z, RULE_OPT, KIND>(a, grid, threads, sh, st, bps);
+    }
+}
+
+template <class F, int KIND>
+static int launch_sliced_family(const SweepArgs& a, int zbytes, int rule, int grid, int threads, size_t sh,
+                                cudaStream_t st, int* bps) {
+    if (zbytes == 1) return launch_sliced_rule<F, uint8_t, KIND>(a, rule, grid, threads, sh, st, bps);
+    if (zbytes == 2) return launch_sliced_rule<F, uint16_t, KIND>(a, rule, grid, threads, sh, st, bps);
+    return launch_sliced_rule<F, uint32_t, KIND>(a, rule, grid, threads, sh, st, bps);
+}
+
 template <class F, class Z, int RULE, int KIND, bool SMEM>
 static int launch_batch_one(const BatchArgs& b, int blocks, int threads, size_t shared_bytes, cudaStream_t st,
                             bool set_attr) {

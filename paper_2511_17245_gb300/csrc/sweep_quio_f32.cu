@@ -10,4 +10,8 @@ int launch_batch_quio_f32(const BatchArgs& b, int zbytes, int rule, bool smem, i
                              size_t sh, void* stream, bool set_attr) {
     return launch_batch_family<float, KIND_QUIO>(b, zbytes, rule, smem, blocks, threads, sh, (cudaStream_t)stream, set_attr);
 }
+int launch_sliced_quio_f32(const SweepArgs& a, int zbytes, int rule, int grid, int threads, size_t sh, void* stream,
+                        int* bps) {
+    return launch_sliced_family<float, KIND_QUIO>(a, zbytes, rule, grid, threads, sh, (cudaStream_t)stream, bps);
+}
 }  // namespace sa

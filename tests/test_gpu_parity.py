@@ -352,3 +352,51 @@ def test_energy_trace_equals_oracle():
                trace_replicas=R)
     assert x["follow"]["mismatch"] == 0
     assert np.array_equal(x["energy_trace"], et.cpu().numpy())
+
+
+# ------------------------------------------------------------------ time-sliced launches
+@pytest.mark.parametrize("rule", ALL_RULES)
+def test_time_sliced_equals_plain_waves(rule):
+    """More replicas than thread groups fit at once (int64 fields of 10,000
+    variables: two replicas per SM): the time-sliced cooperative launch, in
+    which replicas cut between two groups hand their state over, gives the
+    plain waves' results bit for bit, and its traced replicas (replica 1 is
+    split between groups 0 and 1) replay exactly against the oracle."""
+    from paper_2511_17245_gb300 import _lib
+    inst = wl.quio_sparse_int(13, n=10000, n_edges=60000, lo=-30, hi=200, jmax=4, hmax=40, dmax=3)
+    model = Model(inst)
+    om = orc.Model(inst)
+    tmax, tmin = om.auto_temperatures()
+    S, R, TR = 30, 400, 4
+    trace = torch.zeros((S, TR, model.n), dtype=torch.int32, device="cuda")
+    sliced = model.run(rule, S, R, seed=4, t_max=tmax, t_min=tmin, trace=trace, trace_replicas=TR, report=True)
+    plain = model.run(rule, S, R, seed=4, t_max=tmax, t_min=tmin, flags=_lib.SA_FLAG_NO_TIME_SLICING, report=True)
+    torch.cuda.synchronize()
+    assert sliced["report"]["time_sliced"] == 1 and plain["report"]["time_sliced"] == 0, sliced["report"]
+    for key in ("states", "energies", "accepts"):
+        assert torch.equal(sliced[key], plain[key]), key
+    res = _oracle_follow(om, rule, S, 4, tmax, tmin, list(range(TR)), trace.cpu().numpy(), TR)
+    st = sliced["states"].cpu().numpy()
+    en = sliced["energies"].cpu().numpy()
+    for r, x in enumerate(res):
+        assert x["follow"]["mismatch"] == 0, (rule, r, x["follow"])
+        assert np.array_equal(x["states"][0], st[r]) and x["energy"][0] == en[r]
+
+
+def test_time_sliced_float_benchmark_shape():
+    """The 10,000-variable [0,255] fp32 workload with 1024 replicas (the
+    benchmark's shape: 608 resident groups) runs time-sliced; every replica's
+    energy is within 1e-5 of the FP64 recomputation and the energies match the
+    plain waves' by a KS test."""
+    from paper_2511_17245_gb300 import _lib
+    inst = wl.quio_sparse_wide(1)
+    model = Model(inst)
+    tmax, tmin = model.default_temperatures()
+    out = {}
+    for name, flags in (("sliced", 0), ("plain", _lib.SA_FLAG_NO_TIME_SLICING)):
+        out[name] = model.run("heat_bath", 20, 1024, seed=6, t_max=tmax, t_min=tmin, refresh_interval=5,
+                              flags=flags, report=True)
+    assert out["sliced"]["report"]["time_sliced"] == 1
+    e = out["sliced"]["energies"].cpu().numpy()
+    np.testing.assert_allclose(e, model.energy(out["sliced"]["states"]).cpu().numpy(), rtol=1e-5)
+    assert stats.ks_2samp(e, out["plain"]["energies"].cpu().numpy()).pvalue > 0.01

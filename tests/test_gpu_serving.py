@@ -49,7 +49,7 @@ def test_alone_equals_in_mix():
     models = {s["index"]: Model(wl.serving_instance(s)) for s in specs}
     byidx = {s["index"]: s for s in specs}
     probes = [s["index"] for s in specs[:8]]
-    srv = sa_server_create(8 << 30, n_streams=16)
+    srv = sa_server_create(8 << 30, max_running=16)
     try:
         alone = {}
         for k in probes:
@@ -112,7 +112,7 @@ def test_budget_admission_and_backfill():
     models = {s["index"]: Model(wl.serving_instance(s)) for s in specs}
     byidx = {s["index"]: s for s in specs}
     budget = 64 << 20     # a few requests at a time
-    srv = sa_server_create(budget, n_streams=64)
+    srv = sa_server_create(budget, max_running=64)
     try:
         tickets = {k: sa_server_submit(srv, models[k].handle, _params(models[k], byidx[k])) for k in byidx}
         _collect(srv, tickets, models, byidx)
@@ -128,7 +128,7 @@ def test_cancel_timeout_and_rejections():
     big = wl.quio_sparse_wide(5, n=4000, n_edges=30000, lo=0, hi=255)
     m = Model(big)
     small = Model(wl.quio_dense_small(1))
-    srv = sa_server_create(1 << 30, n_streams=1)
+    srv = sa_server_create(1 << 30, max_running=1)
     try:
         long_p = make_params("heat_bath", 400, 256, seed=1)
         t_long = sa_server_submit(srv, m.handle, long_p)
@@ -153,3 +153,49 @@ def test_cancel_timeout_and_rejections():
         assert e.value.status == _lib.SA_ERR_UNSUPPORTED
     finally:
         sa_server_destroy(srv)
+
+
+def test_serving_variants_equal_sa_run():
+    """Requests that take the serving kernel's other paths, all in one mix: a
+    replica state too large for a shared-memory region (N = 20,000 with int64
+    fields: state slab in global memory), 4-byte state offsets (range width
+    100,000), float HUIO and every rule.  Integer results equal sa_run's bit
+    for bit; float results are within 1e-5 of an FP64 recomputation."""
+    cases = [
+        (wl.quio_sparse_int(31, n=20000, n_edges=60000, lo=-3, hi=9, jmax=3, hmax=20, dmax=2), "metropolis", 6, 8),
+        (wl.quio_sparse_int(32, n=300, n_edges=900, lo=-50000, hi=50000, jmax=2, hmax=30, dmax=1), "heat_bath", 5, 6),
+        (wl.quio_sparse_int(33, n=300, n_edges=900, lo=-50000, hi=50000, jmax=2, hmax=30, dmax=1), "opt_metropolis", 20, 6),
+        (wl.random_interaction(50, 3, 6, n_terms=300, seed=7, integer=False), "heat_bath", 30, 16),
+        (wl.random_interaction(50, 4, 5, n_terms=300, seed=8, integer=True, int_scale=9), "opt_metropolis", 40, 16),
+        (wl.huio_zipf(9, n=400, n_quad=800, n_cubic=1000, n_quartic=200, lo=-7, hi=7), "heat_bath", 30, 12),
+    ]
+    models = [Model(c[0]) for c in cases]
+    srv = sa_server_create(8 << 30, max_running=64)
+    try:
+        tickets = []
+        for (inst, rule, S, R), m in zip(cases, models):
+            tmax, tmin = m.default_temperatures()
+            tickets.append(sa_server_submit(srv, m.handle, make_params(rule, S, R, seed=3, t_max=tmax, t_min=tmin)))
+        got = []
+        for t, (inst, rule, S, R), m in zip(tickets, cases, models):
+            sa_server_wait(srv, t, 300_000_000)
+            st = np.zeros((R, m.n), np.int32)
+            en = np.zeros(R, np.float64 if m.is_float else np.int64)
+            ac = np.zeros(R, np.uint64)
+            sa_server_result(srv, t, st, en, ac)
+            got.append((st, en, ac))
+        stats_ = sa_server_get_stats(srv)
+        assert stats_["completed"] == len(cases) and stats_["failed"] == 0
+        assert stats_["units_done"] == sum(c[3] for c in cases) and stats_["kernel_launches"] >= 1
+    finally:
+        sa_server_destroy(srv)
+    for (inst, rule, S, R), m, (st, en, ac) in zip(cases, models, got):
+        tmax, tmin = m.default_temperatures()
+        one = m.run(rule, S, R, seed=3, t_max=tmax, t_min=tmin)
+        if m.is_float:
+            e = m.energy(torch.from_numpy(st).cuda()).cpu().numpy()
+            np.testing.assert_allclose(en, e, rtol=1e-5, atol=1e-6)
+        else:
+            assert np.array_equal(st, one["states"].cpu().numpy()), rule
+            assert np.array_equal(en, one["energies"].cpu().numpy()), rule
+            assert np.array_equal(ac.astype(np.int64), one["accepts"].cpu().numpy()), rule

@@ -107,47 +107,37 @@ def test_plan_schedule_closed_form(tmp_path):
     assert out[17:19] == [1, 1]
 
 
-@pytest.mark.parametrize("R,S,P", [(1024, 100, 608), (1024, 7, 608), (700, 50, 608), (609, 3, 608),
-                                   (5000, 20, 152), (61, 13, 60), (10, 1, 3), (608, 9, 608)])
-def test_slice_plan_covers_every_sweep_once(tmp_path, R, S, P):
-    """Time-sliced schedule: every (replica, sweep) pair is run by exactly one
-    slot, each replica's pieces are contiguous and in sweep order, a split
-    replica's head is the last piece group of slot p and its tail the first of
-    slot p + 1, and the head ends no later (in the slot's own sweep count)
-    than the tail starts."""
-    Q = -(-R * S // P)
-    body = f"""
-  for (int p = 0; p < {P}; ++p) {{
-    sa::SlicePlan sp = sa::slice_plan(p, {R}, {S}, {P}LL);
-    std::printf("%d %d %d %d %d %d %d %d %d %d %d\\n", p, sp.has_head, sp.head.r, sp.head.s0, sp.head.s1,
-                sp.whole_r0, sp.whole_r1, sp.has_tail, sp.tail.r, sp.tail.s0, sp.tail.s1);
-  }}
-"""
-    out = [int(x) for x in _compile_and_run(tmp_path, body)]
-    rows = [out[i:i + 11] for i in range(0, 11 * P, 11)]
-    seen = {}
-    for p, hh, hr, h0, h1, w0, w1, ht, tr, t0, t1 in rows:
-        order = []          # the slot's own execution order: head, whole, tail
-        if hh:
-            order.append((hr, h0, h1))
-        order += [(r, 0, S) for r in range(w0, w1)]
-        if ht:
-            order.append((tr, t0, t1))
-        assert sum(b - a for _, a, b in order) <= Q
-        clock = 0
-        for r, a, b in order:
-            assert 0 <= a < b <= S
-            for s in range(a, b):
-                assert (r, s) not in seen
-                seen[(r, s)] = (p, clock + (s - a))
-            clock += b - a
+@pytest.mark.parametrize("R,S,P", [(1024, 1000, 608), (1024, 7, 608), (700, 50, 608), (609, 3, 608),
+                                   (5000, 200, 152), (61, 13, 60), (10, 1, 3)])
+def test_time_sliced_tasks_cover_every_sweep_once(tmp_path, R, S, P):
+    """Time-sliced launch: the chunk-major tasks cover every (replica, sweep)
+    pair exactly once in chunks of at most S/16 sweeps, and greedy claiming by
+    P groups, simulated with sweeps that cost three times more in the first
+    third of the schedule, ends within the list-scheduling bound (total work /
+    P + one chunk per dependency wait) and no later than plain waves."""
+    import heapq
+    out = _compile_and_run(tmp_path, f'  std::printf("%d\\n", sa::slice_chunk_sweeps({S}));')
+    K = int(out[0])
+    C = -(-S // K)
+    assert C <= 16 and (C - 1) * K < S <= C * K
+    cost = [3.0 if s < S // 3 else 1.0 for s in range(S)]
+    seen = set()
+    finish = {}
+    heap = [(0.0, p) for p in range(P)]
+    for q in range(R * C):
+        j, r = divmod(q, R)
+        s0, s1 = j * K, min(S, (j + 1) * K)
+        for s in range(s0, s1):
+            assert (r, s) not in seen
+            seen.add((r, s))
+        t, p = heapq.heappop(heap)
+        start = max(t, finish.get((r, j - 1), 0.0))
+        finish[(r, j)] = start + sum(cost[s0:s1])
+        heapq.heappush(heap, (finish[(r, j)], p))
     assert len(seen) == R * S
-    for r in range(R):
-        slots = [seen[(r, s)] for s in range(S)]
-        ps = sorted({x[0] for x in slots})
-        assert len(ps) <= 2 and (len(ps) == 1 or ps[1] == ps[0] + 1)
-        if len(ps) == 2:
-            # head on ps[0] (sweeps 0..), tail on ps[1]; head finishes before the tail starts
-            head = [t for (p, t) in slots if p == ps[0]]
-            tail = [t for (p, t) in slots if p == ps[1]]
-            assert slots[0][0] == ps[0] and max(head) < min(tail)
+    makespan = max(finish.values())
+    per_replica = sum(cost)
+    max_chunk = max(sum(cost[j * K:(j + 1) * K]) for j in range(C))
+    assert makespan <= R * per_replica / P + 2 * max_chunk + 1e-9
+    waves = -(-R // P)
+    assert makespan <= waves * per_replica + 1e-9
