@@ -152,6 +152,7 @@ typedef struct {
 /* Run flags */
 #define SA_FLAG_STATE_IN_GLOBAL 0x1   /* keep per-replica state in global memory even if it fits on chip */
 #define SA_FLAG_NO_TIME_SLICING 0x2   /* run more replicas than fit at once as plain waves (see sa_run) */
+#define SA_FLAG_NO_SPECULATION  0x4   /* decide single-variable levels one at a time (see sa_run) */
 
 typedef struct {
     int32_t rule;                 /* sa_rule                                              */
@@ -196,6 +197,17 @@ typedef struct {
  * (Sect. 3.1).  The kernels run the updates of variables that share no term
  * concurrently when they form a dependency level; this reproduces the
  * sequential trajectory exactly for integer models.
+ *
+ * Speculative windows (QUIO): a run of levels that hold one variable each
+ * (every level of a complete graph) is decided by the lanes of one warp, up
+ * to 32 levels at once.  The decisions before the first one that changes its
+ * variable saw the same state as in the sequential order, and so did that
+ * one; its neighbours' fields are then updated and the next window starts
+ * after it.  States, energies, counts and traces are those of the
+ * level-by-level order, bit for bit (float models included).  Float heat bath,
+ * and heat bath where a variable's range makes the kernel decide it with a
+ * whole warp, keep the level-by-level order.  SA_FLAG_NO_SPECULATION disables
+ * the windows.
  *
  * Time slicing: when the replicas' state stays in shared memory but more
  * replicas are requested than thread groups fit on the GPU at once, and the
@@ -292,8 +304,9 @@ void sa_batch_destroy(sa_batch* batch);
  * sa_model_destroy) from other threads wait until the server has drained.
  *
  * sa_server_create  budget_bytes > 0; max_running in 1..8192 (requests admitted
- *                   at a time); threads_per_replica 0 (128), 64, 128 or 256:
- *                   the thread-group size of the serving kernel.
+ *                   at a time); threads_per_replica 0 (256), 64, 128 or 256:
+ *                   the thread-group size of the serving kernel (two groups
+ *                   of 256 per SM, each with a ~112 KB state region, by default).
  * sa_server_submit  copies params (and params->temperatures); trace,
  *                   energy_trace, report and init_states must be NULL.  The model
  *                   must stay alive until the request is finished.  A request

@@ -25,6 +25,7 @@ COEF = {"i32": 0, "i64": 1, "f32": 2, "f64": 3}
 RULES = {"metropolis": 0, "heat_bath": 1, "opt_metropolis": 2}
 SA_FLAG_STATE_IN_GLOBAL = 0x1
 SA_FLAG_NO_TIME_SLICING = 0x2
+SA_FLAG_NO_SPECULATION = 0x4
 
 
 class SAError(RuntimeError):

@@ -259,7 +259,7 @@ sa_status compile_terms(sa_model* M, int32_t n, const int64_t* lower, const int6
     struct Offs {
         size_t meta, lvl_ptr, lvl_vars, lvl_rec;
         size_t adj_col, adj_i, adj_f, adj_d, lin_i, lin_f, lin_d, diag_i, diag_f, diag_d;
-        size_t slot_base, omega, aconst_i, aconst_f, aconst_d, inc_term, inc_exp, term_ptr, mem_var, mem_exp,
+        size_t slot_base, omega, aconst_i, aconst_f, aconst_d, inc_term, inc_exp, inc_rec, term_ptr, mem_var, mem_exp,
             tcoef_i, tcoef_f, tcoef_d;
     } off{};
     std::vector<int32_t> lvl_ptr, lvl_vars;
@@ -313,6 +313,10 @@ sa_status compile_terms(sa_model* M, int32_t n, const int64_t* lower, const int6
         }
         M->n_links = 0;
         for (int32_t k = 0; k < n; ++k) M->n_links += deg[k];
+        // complete graph: rows are sorted, so row k lists 0..k-1, k+1..n-1
+        dm.dense_rows = 1;
+        for (int32_t k = 0; k < n && dm.dense_rows; ++k)
+            if (deg[k] != n - 1) dm.dense_rows = 0;
         // neighbour lists for the levels (without padding)
         nb_ptr.assign(n + 1, 0);
         for (int32_t k = 0; k < n; ++k) nb_ptr[k + 1] = nb_ptr[k] + deg[k];
@@ -422,6 +426,32 @@ sa_status compile_terms(sa_model* M, int32_t n, const int64_t* lower, const int6
             M->max_link_len = std::max(M->max_link_len, meta[k].link_len);
         }
         M->n_links = iptr[n];
+        // incidence records: everything one cache update of Eq. energy_diff_upd
+        // needs for a term of at most 4 members, read in one step
+        std::vector<int32_t> inc_rec((size_t)iptr[n] * 12, 0);
+        for (int32_t k = 0; k < n; ++k)
+            for (int64_t e = iptr[k]; e < iptr[k + 1]; ++e) {
+                int32_t* q = inc_rec.data() + (size_t)e * 12;
+                const int32_t tt = inc_term[e];
+                const int32_t nm = term_ptr[tt + 1] - term_ptr[tt];
+                q[0] = tt;
+                q[1] = inc_exp[e];
+                if (nm > 4) {
+                    q[2] = -1;
+                    continue;
+                }
+                int c = 0, packed = 0;
+                for (int32_t p = term_ptr[tt]; p < term_ptr[tt + 1]; ++p) {
+                    const int32_t v = mem_var[p];
+                    if (v == k) continue;
+                    q[4 + c] = v;
+                    packed |= mem_exp[p] << (8 * c);
+                    q[8 + c] = slot_of(v, mem_exp[p]);
+                    ++c;
+                }
+                q[2] = c;
+                q[7] = packed;
+            }
         // neighbours for levels: members of incident interaction terms
         nb_ptr.assign(n + 1, 0);
         for (int32_t k = 0; k < n; ++k) {
@@ -461,6 +491,7 @@ sa_status compile_terms(sa_model* M, int32_t n, const int64_t* lower, const int6
         off.omega = blob.add(omega);
         off.inc_term = blob.add(inc_term);
         off.inc_exp = blob.add(inc_exp);
+        off.inc_rec = blob.add(inc_rec);
         off.term_ptr = blob.add(term_ptr);
         off.mem_var = blob.add(mem_var);
         off.mem_exp = blob.add(mem_exp);
@@ -506,6 +537,7 @@ sa_status compile_terms(sa_model* M, int32_t n, const int64_t* lower, const int6
         dm.omega = at<uint64_t>(b, off.omega);
         dm.inc_term = at<int32_t>(b, off.inc_term);
         dm.inc_exp = at<int32_t>(b, off.inc_exp);
+        dm.inc_rec = at<int32_t>(b, off.inc_rec);
         dm.term_ptr = at<int32_t>(b, off.term_ptr);
         dm.mem_var = at<int32_t>(b, off.mem_var);
         dm.mem_exp = at<int32_t>(b, off.mem_exp);
@@ -831,6 +863,7 @@ sa_status sa_run(const sa_model* M, const sa_run_params* p, int32_t* out_states,
     a.key1 = (uint32_t)(p->seed >> 32);
     a.inst = p->instance_id;
     a.refresh_interval = p->refresh_interval > 0 ? p->refresh_interval : 50;
+    a.speculate = (p->flags & SA_FLAG_NO_SPECULATION) ? 0 : 1;
     a.beta = d_tab;
     a.ratio = d_tab + S;
     a.init_states = d_init;

@@ -282,6 +282,7 @@ sa_status sa_batch_create(sa_batch** out, const sa_model* const* models, int32_t
         a.key1 = (uint32_t)(p.seed >> 32);
         a.inst = p.instance_id;
         a.refresh_interval = p.refresh_interval > 0 ? p.refresh_interval : 50;
+        a.speculate = (p.flags & SA_FLAG_NO_SPECULATION) ? 0 : 1;
         a.beta = d_tab + tpos;
         a.ratio = d_tab + tpos + S;
         a.init_states = p.init_states;

@@ -127,6 +127,7 @@ extern "C" sa_status sa_run_noalloc(const sa_model* M, const sa_run_params* p, i
     a.key1 = (uint32_t)(p->seed >> 32);
     a.inst = p->instance_id;
     a.refresh_interval = p->refresh_interval > 0 ? p->refresh_interval : 50;
+    a.speculate = (p->flags & SA_FLAG_NO_SPECULATION) ? 0 : 1;
     a.beta = d_tab;
     a.ratio = d_tab + S;
     a.init_states = p->init_states;

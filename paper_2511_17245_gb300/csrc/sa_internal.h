@@ -41,7 +41,7 @@ struct DevModel {
     int32_t is_float;
     int32_t n_levels;
     uint32_t max_width;         // largest u_k - l_k
-    int32_t _pad0;
+    int32_t dense_rows;         // QUIO on a complete graph: row k lists every j != k in increasing order
     const VarMeta* meta;        // [n]
     const int32_t* lvl_ptr;     // [n_levels + 1]
     const int32_t* lvl_vars;    // [n]: variables grouped by dependency level
@@ -70,6 +70,12 @@ struct DevModel {
     const double* aconst_d;
     const int32_t* inc_term;    // incidence of variable s: interaction terms containing s
     const int32_t* inc_exp;     //   and the exponent of s in that term
+    // per incidence, 12 int32 (three 16-byte groups): {term, exponent of s,
+    // number of other members (0..3, or -1 for terms of more than 4 members),
+    // 0}, {other members' variables v1..v3, their exponents packed
+    // e1 | e2 << 8 | e3 << 16}, {their coefficient slots (slot_base[v] + index
+    // of the exponent), 0}
+    const int32_t* inc_rec;
     const int32_t* term_ptr;    // [n_iterms + 1] into mem_var / mem_exp
     const int32_t* mem_var;     // members (distinct variables) of interaction terms
     const int32_t* mem_exp;     // their exponents
@@ -105,6 +111,8 @@ struct SweepArgs {
     int64_t rep_bytes;          // bytes of one replica's state region
     int32_t off_z, off_cache, off_ctl, off_list, off_red;
     int32_t off_lvl;            // level boundaries staged in the replica region (-1: read from the model)
+    int32_t speculate;          // decide runs of single-variable levels a warp at a time
+    int32_t _pad_spec;
     int32_t rpc;                // replicas per block
     int32_t tpr;                // threads per replica (multiple of 32)
     int32_t heavy_links;        // link_len above which updates are cooperative
@@ -255,8 +263,9 @@ struct RunPlan {
 inline int64_t plan_round16(int64_t x) { return (x + 15) / 16 * 16; }
 
 // State layout of one replica for `tpr` threads: offsets z_k - l_k (zbytes
-// each), the cache (int64 or fp32), three list counters plus the flattened
-// length, the cooperative update list, the reduction scratch (one 8-byte word
+// each), the cache (int64 or fp32), the control words (three list counters,
+// the flattened length and two 48-byte results of speculative windows), the
+// cooperative update list, the reduction scratch (one 8-byte word
 // per warp) and, when it takes at most 16 KB, the level boundary table.
 // `zbytes` may exceed the model's own (a batch uses its widest).  QUIO rows are
 // cheap per entry (one atomic) and go inline up to 64 links; HUIO incidences
@@ -270,7 +279,7 @@ inline int64_t plan_layout(const PlanModel& m, int zbytes, int tpr, RunPlan* p) 
     p->off_z = 0;
     p->off_cache = (int32_t)plan_round16((int64_t)m.n * zbytes);
     p->off_ctl = (int32_t)plan_round16(p->off_cache + m.cache_elems * fsize);
-    p->off_list = p->off_ctl + 16;
+    p->off_list = p->off_ctl + 112;
     p->off_red = (int32_t)plan_round16(p->off_list + (int64_t)p->list_cap * 24);
     const int64_t lvl_bytes = (int64_t)(m.n_levels + 1) * 4;
     const int64_t off_lvl = plan_round16(p->off_red + (int64_t)(tpr / 32) * 8);

@@ -175,6 +175,7 @@ bool admit(sa_server* s, Request* r, int slot) {
     a.key1 = (uint32_t)(p.seed >> 32);
     a.inst = p.instance_id;
     a.refresh_interval = p.refresh_interval > 0 ? p.refresh_interval : 50;
+    a.speculate = (p.flags & SA_FLAG_NO_SPECULATION) ? 0 : 1;
     a.beta = reinterpret_cast<const float*>(d + r->o_tab);
     a.ratio = a.beta + S;
     a.out_states = reinterpret_cast<int32_t*>(d + o_st);
@@ -368,7 +369,7 @@ sa_status sa_server_create(sa_server** out, const sa_server_config* cfg) {
     *out = nullptr;
     if (cfg->budget_bytes == 0 || cfg->max_running < 1 || cfg->max_running > kMaxRunning)
         return sfail(SA_ERR_INVALID, "budget must be positive and max_running in 1..8192");
-    const int tpr = cfg->threads_per_replica > 0 ? cfg->threads_per_replica : 128;
+    const int tpr = cfg->threads_per_replica > 0 ? cfg->threads_per_replica : 256;
     if (tpr != 64 && tpr != 128 && tpr != 256) return sfail(SA_ERR_INVALID, "threads_per_replica must be 0, 64, 128 or 256");
     sa_server* s = new sa_server();
     s->cfg = *cfg;

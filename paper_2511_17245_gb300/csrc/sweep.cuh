@@ -713,14 +713,24 @@ __device__ __forceinline__ long long heat_bath_quio_f32_small(float f, float d, 
         sel = nrb - 1;
         run = before_last;
     }
+    // the chosen block: its weights first (independent exp2), then the
+    // smallest value whose running sum reaches the threshold
     const int first = base + sel * 16;
-    const int last = min(first + 15, n - 1);
+    const int cnt = min(16, n - first);
     const float a0 = dz0 + (float)first;
-    for (int j = 0; j <= last - first; ++j) {
-        run += quio_w(a0 + (float)j, hA, hB, mb);
-        if (run >= thr) return lo + (long long)(first + j);
+    float w[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) w[j] = j < cnt ? quio_w(a0 + (float)j, hA, hB, mb) : 0.f;
+    int pick = cnt - 1;
+    bool found = false;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        run += w[j];
+        const bool hit = !found && j < cnt && run >= thr;
+        pick = hit ? j : pick;
+        found = found || hit;
     }
-    return lo + (long long)last;
+    return lo + (long long)(first + pick);
 }
 
 // Multilinear variable, dE = a (v - z): P(i) proportional to exp(-lambda i) on
@@ -944,50 +954,120 @@ __device__ __forceinline__ void quio_update_row(const DevModel& m, F* cache, int
 // HUIO (Eq. energy_diff_upd): for every interaction term t containing s with
 // exponent e_s, and every other member k with exponent e_k,
 //   a_k^(e_k) += J_t ((z_s')^{e_s} - z_s^{e_s}) prod_{i in t \ {k, s}} z_i^{e_i}.
+// One incidence e of s: the term's members (at most kTermRegs) are read once
+// into registers through the read-only path, the products over the other
+// members come from prefix and suffix products, and the model loads of
+// consecutive incidences do not wait on the previous incidence's atomics.
+constexpr int kTermRegs = 8;
+
+template <class F, class Z>
+__device__ __forceinline__ void huio_update_one(const DevModel& m, const Z* zs, F* cache, int s, int e,
+                                                long long z_old, long long z_new) {
+    const int4* rec = reinterpret_cast<const int4*>(m.inc_rec) + 3 * (size_t)e;
+    const int4 r0 = __ldg(rec);
+    if (r0.z >= 0) {
+        // term of at most 4 members: its record holds the other members and
+        // their slots, so the z values, bounds and coefficient load together
+        const int4 r1 = __ldg(rec + 1), r2 = __ldg(rec + 2);
+        const int no = r0.z, es = r0.y, ep = r1.w;
+        const int vv[3] = {r1.x, r1.y, r1.z};
+        const int sl[3] = {r2.x, r2.y, r2.z};
+        F base;
+        if constexpr (Num<F>::is_float)
+            base = Coef<float>::tcoef(m, r0.x) * (ipow<float>((float)z_new, es) - ipow<float>((float)z_old, es));
+        else base = __ldg(m.tcoef_i + r0.x) * (ipow<long long>(z_new, es) - ipow<long long>(z_old, es));
+        F zp[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            zp[i] = F(1);
+            if (i < no) {
+                const long long zv = (long long)__ldg(&m.meta[vv[i]].lo) + (long long)zs[vv[i]];
+                const int ex = (ep >> (8 * i)) & 0xFF;
+                if constexpr (Num<F>::is_float) zp[i] = ipow<float>((float)zv, ex);
+                else zp[i] = ipow<long long>(zv, ex);
+            }
+        }
+        // member i receives base times the other members' powers
+        if (no > 0) atomic_add_field(cache + sl[0], base * zp[1] * zp[2]);
+        if (no > 1) atomic_add_field(cache + sl[1], base * zp[0] * zp[2]);
+        if (no > 2) atomic_add_field(cache + sl[2], base * zp[0] * zp[1]);
+        return;
+    }
+    const int tt = r0.x;
+    const int es = r0.y;
+    const int p0 = __ldg(m.term_ptr + tt), p1 = __ldg(m.term_ptr + tt + 1);
+    const int nm = p1 - p0;
+    F base;
+    if constexpr (Num<F>::is_float) base = Coef<float>::tcoef(m, tt) * (ipow<float>((float)z_new, es) - ipow<float>((float)z_old, es));
+    else base = __ldg(m.tcoef_i + tt) * (ipow<long long>(z_new, es) - ipow<long long>(z_old, es));
+    if (nm <= kTermRegs) {
+        int var[kTermRegs], ex[kTermRegs];
+        F zp[kTermRegs];
+#pragma unroll
+        for (int i = 0; i < kTermRegs; ++i) {
+            if (i < nm) {
+                var[i] = __ldg(m.mem_var + p0 + i);
+                ex[i] = __ldg(m.mem_exp + p0 + i);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kTermRegs; ++i) {
+            zp[i] = F(1);
+            if (i < nm && var[i] != s) {
+                const long long zv = (long long)__ldg(&m.meta[var[i]].lo) + (long long)zs[var[i]];
+                if constexpr (Num<F>::is_float) zp[i] = ipow<float>((float)zv, ex[i]);
+                else zp[i] = ipow<long long>(zv, ex[i]);
+            }
+        }
+        // suffix products: suf[i] = prod_{j >= i} zp[j]
+        F suf[kTermRegs + 1];
+        suf[kTermRegs] = F(1);
+#pragma unroll
+        for (int i = kTermRegs - 1; i >= 0; --i) suf[i] = suf[i + 1] * zp[i];
+        F pre = base;
+#pragma unroll
+        for (int i = 0; i < kTermRegs; ++i) {
+            if (i < nm && var[i] != s) {
+                const int k = var[i];
+                const uint64_t om = __ldg(m.omega + k);
+                const int q = __popcll((om & ((1ull << ex[i]) - 1ull)) >> 1);
+                atomic_add_field(cache + __ldg(m.slot_base + k) + q, pre * suf[i + 1]);
+            }
+            pre *= zp[i];
+        }
+        return;
+    }
+    for (int pk = p0; pk < p1; ++pk) {
+        const int k = __ldg(m.mem_var + pk);
+        if (k == s) continue;
+        F prod = base;
+        for (int pi = p0; pi < p1; ++pi) {
+            const int v = __ldg(m.mem_var + pi);
+            if (v == s || v == k) continue;
+            const long long zv = (long long)__ldg(&m.meta[v].lo) + (long long)zs[v];
+            if constexpr (Num<F>::is_float) prod *= ipow<float>((float)zv, __ldg(m.mem_exp + pi));
+            else prod *= ipow<long long>(zv, __ldg(m.mem_exp + pi));
+        }
+        const uint64_t om = __ldg(m.omega + k);
+        const int ek = __ldg(m.mem_exp + pk);
+        const int q = __popcll((om & ((1ull << ek) - 1ull)) >> 1);
+        atomic_add_field(cache + __ldg(m.slot_base + k) + q, prod);
+    }
+}
+
 template <class F, class Z>
 __device__ __forceinline__ void huio_update_range(const DevModel& m, const Z* zs, F* cache, int s, int begin,
                                                   int end, int stride, long long z_old, long long z_new) {
-    for (int e = begin; e < end; e += stride) {
-        const int tt = m.inc_term[e];
-        const int es = m.inc_exp[e];
-        const int p0 = m.term_ptr[tt], p1 = m.term_ptr[tt + 1];
-        if constexpr (Num<F>::is_float) {
-            const float dpow = ipow<float>((float)z_new, es) - ipow<float>((float)z_old, es);
-            const float base = Coef<float>::tcoef(m, tt) * dpow;
-            for (int pk = p0; pk < p1; ++pk) {
-                const int k = m.mem_var[pk];
-                if (k == s) continue;
-                float prod = base;
-                for (int pi = p0; pi < p1; ++pi) {
-                    const int v = m.mem_var[pi];
-                    if (v == s || v == k) continue;
-                    prod *= ipow<float>((float)((long long)m.meta[v].lo + (long long)zs[v]), m.mem_exp[pi]);
-                }
-                const uint64_t om = m.omega[k];
-                const int ek = m.mem_exp[pk];
-                const int q = __popcll((om & ((1ull << ek) - 1ull)) >> 1);
-                atomic_add_field(cache + m.slot_base[k] + q, prod);
-            }
-        } else {
-            const long long dpow = ipow<long long>(z_new, es) - ipow<long long>(z_old, es);
-            const long long base = m.tcoef_i[tt] * dpow;
-            for (int pk = p0; pk < p1; ++pk) {
-                const int k = m.mem_var[pk];
-                if (k == s) continue;
-                long long prod = base;
-                for (int pi = p0; pi < p1; ++pi) {
-                    const int v = m.mem_var[pi];
-                    if (v == s || v == k) continue;
-                    prod *= ipow<long long>((long long)m.meta[v].lo + (long long)zs[v], m.mem_exp[pi]);
-                }
-                const uint64_t om = m.omega[k];
-                const int ek = m.mem_exp[pk];
-                const int q = __popcll((om & ((1ull << ek) - 1ull)) >> 1);
-                atomic_add_field(cache + m.slot_base[k] + q, prod);
-            }
-        }
-    }
+    for (int e = begin; e < end; e += stride) huio_update_one<F, Z>(m, zs, cache, s, e, z_old, z_new);
 }
+
+// Field update of a level's only variable (no other writer): rounded product,
+// then rounded sum, at every call site, so that every schedule of the same
+// updates gives the same fp32 fields.
+__device__ __forceinline__ void solo_add(float* c, float w, long long dz) {
+    *c = __fadd_rn(*c, __fmul_rn(w, (float)(int)dz));
+}
+__device__ __forceinline__ void solo_add(long long* c, long long w, long long dz) { *c += w * dz; }
 
 // ------------------------------------------------------------------ reductions
 template <class T>
@@ -1030,7 +1110,8 @@ __device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot,
     if (s1 < 0) s1 = a.S;
     Z* zs = reinterpret_cast<Z*>(base + a.off_z);
     F* cache = reinterpret_cast<F*>(base + a.off_cache);
-    int* ctl = reinterpret_cast<int*>(base + a.off_ctl);      // [3] list counters, [3] flattened length
+    // [0..2] list counters, [3] flattened length, [4..27] two results of speculative windows
+    int* ctl = reinterpret_cast<int*>(base + a.off_ctl);
     // [cap][6]: variable k, z_old, z_new, link_begin, link_len, prefix of the
     // flattened (entry, link) pairs
     int* list = reinterpret_cast<int*>(base + a.off_list);
@@ -1041,7 +1122,6 @@ __device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot,
     int* lvl_s = a.off_lvl >= 0 ? reinterpret_cast<int*>(base + a.off_lvl) : nullptr;
     if (lvl_s)
         for (int L = t; L <= m.n_levels; L += tpr) lvl_s[L] = __ldg(m.lvl_ptr + L);
-
     float drift = 0.f;
     Acc eacc;
     unsigned long long changes = 0;
@@ -1194,7 +1274,7 @@ __device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot,
         for (int i = b0 + t; i < b1; i += tpr) prefetch_l1(m.lvl_rec + i);
     };
     prefetch_level(0);
-
+    int win = 0;   // speculative windows run so far (their result slots alternate)
     for (int s = s0; s < s1; ++s) {
         const float beta = __ldg(a.beta + s);
         const float temp = 1.f / beta;
@@ -1203,6 +1283,108 @@ __device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot,
             int* cnt_now = ctl + gl3;
             if (t == 0) ctl[gl3 == 2 ? 0 : gl3 + 1] = 0;
             const int lb = lvl_at(L), le = lvl_at(L + 1);
+            // heat bath over wide ranges gives a narrow level's variables a warp each
+            bool wmode = false;
+            if constexpr (RULE == RULE_HEAT_BATH)
+                wmode = hb_warp_mode(le - lb, tpr, m.max_width,
+                                     Num<F>::is_float && KIND == KIND_QUIO && m.max_width < 256u);
+            // (QUIO only, and neither float heat bath nor heat bath in warp mode:
+            // second inlined copies of their decision or update code would make
+            // the kernel spill registers)
+            constexpr bool kSpeculative = KIND == KIND_QUIO && !(RULE == RULE_HEAT_BATH && Num<F>::is_float);
+            if constexpr (kSpeculative) if (a.speculate && le - lb == 1 && !wmode) {
+                // ---- a run of single-variable levels (every level of a complete
+                // graph), decided by the lanes of warp 0, up to 32 levels at a
+                // time, lane i deciding level L + i.  Every decision before the first one that changes
+                // its variable saw the state of the level-by-level order, since
+                // nothing changed before it, and so did that one; the group then
+                // updates that variable's neighbours and the next window starts
+                // after it.  Results equal those of the level-by-level order; the
+                // energy change and the count go to thread 0 as they do there.
+                int* res = ctl + 4 + 12 * (win & 1);   // {k or -1, levels done, row begin, row length,
+                                                      //  z_old (2), z_new (2), dE (2)}
+                if (t < 32) {
+                    const int lane = t;
+                    const int Li = L + lane;
+                    int idx = 0;
+                    bool single = false;
+                    if (Li < m.n_levels) {
+                        idx = lvl_at(Li);
+                        single = lvl_at(Li + 1) - idx == 1;
+                    }
+                    const unsigned multi = __ballot_sync(0xffffffffu, !single);
+                    const int w = multi ? __ffs(multi) - 1 : 32;   // >= 1: level L holds one variable
+                    long long zz = 0, vv2 = 0;
+                    F d2 = F(0);
+                    LevelRec rc{};
+                    int p = w;           // levels decided without a change
+                    bool chg = false;    // level L + p changed its variable
+                    if (lane < w) {
+                        rc = load_rec(idx);
+                        decide(rc, s, beta, temp, ratio, zz, vv2, d2, false);
+                    }
+                    {
+                        const unsigned c = __ballot_sync(0xffffffffu, lane < w && vv2 != zz);
+                        if (c) {
+                            p = __ffs(c) - 1;
+                            chg = true;
+                        }
+                        if (a.trace != nullptr && r < a.trace_R && (lane < p || (chg && lane == p)))
+                            a.trace[((size_t)s * a.trace_R + r) * m.n + rc.k] = (int32_t)vv2;
+                        // the changing lane's decision goes to lane 0
+                        if (chg) {
+                            const int k2 = __shfl_sync(0xffffffffu, rc.k, p);
+                            const int lo2 = __shfl_sync(0xffffffffu, rc.lo, p);
+                            const int b2 = __shfl_sync(0xffffffffu, rc.link_begin, p);
+                            const int l2 = __shfl_sync(0xffffffffu, rc.link_len, p);
+                            zz = __shfl_sync(0xffffffffu, zz, p);
+                            vv2 = __shfl_sync(0xffffffffu, vv2, p);
+                            d2 = __shfl_sync(0xffffffffu, d2, p);
+                            rc.k = k2;
+                            rc.lo = lo2;
+                            rc.link_begin = b2;
+                            rc.link_len = l2;
+                        }
+                    }
+                    if (lane == 0) {
+                        res[0] = chg ? rc.k : -1;
+                        res[1] = chg ? p + 1 : w;
+                        if (chg) {
+                            zs[rc.k] = (Z)(vv2 - (long long)rc.lo);
+                            res[2] = rc.link_begin;
+                            res[3] = rc.link_len;
+                            *reinterpret_cast<long long*>(res + 4) = zz;
+                            *reinterpret_cast<long long*>(res + 6) = vv2;
+                            *reinterpret_cast<F*>(res + 8) = d2;
+                        }
+                    }
+                }
+                named_bar(bar_id, tpr);
+                const int kk = res[0];
+                if (kk >= 0) {
+                    const int rb = res[2], rl = res[3];
+                    const long long zold = *reinterpret_cast<const long long*>(res + 4);
+                    const long long znew = *reinterpret_cast<const long long*>(res + 6);
+                    if (t == 0) {
+                        if constexpr (Num<F>::is_float) dacc += (float)*reinterpret_cast<const F*>(res + 8);
+                        else eacc += (Acc)*reinterpret_cast<const F*>(res + 8);
+                        ++changes;
+                    }
+                    if (m.dense_rows) {
+                        // row kk lists every j != kk in order: its columns need no reads
+                        for (int e = t; e < rl; e += tpr)
+                            solo_add(cache + e + (e >= kk ? 1 : 0), Coef<F>::adj(m, rb + e), znew - zold);
+                    } else {
+                        for (int e = rb + t; e < rb + rl; e += tpr)
+                            solo_add(cache + __ldg(m.adj_col + e), Coef<F>::adj(m, e), znew - zold);
+                    }
+                    named_bar(bar_id, tpr);
+                }
+                L += res[1] - 1;
+                ++win;
+                gl3 = gl3 == 2 ? 0 : gl3 + 1;
+                continue;
+            }
             // the next level (the first level of the next sweep after the last)
             if (L + 1 < m.n_levels) prefetch_level(L + 1);
             else if (s + 1 < a.S) prefetch_level(0);
@@ -1211,10 +1393,6 @@ __device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot,
             // bath over wide ranges or narrow levels gives each variable a warp
             const int lane = t & 31;
             const bool solo = le - lb == 1;
-            bool wmode = false;
-            if constexpr (RULE == RULE_HEAT_BATH)
-                wmode = hb_warp_mode(le - lb, tpr, m.max_width,
-                                     Num<F>::is_float && KIND == KIND_QUIO && m.max_width < 256u);
             const int per_round = wmode ? (tpr >> 5) : tpr;
             const int slot_i = wmode ? (t >> 5) : t;
             const int rounds = (le - lb + per_round - 1) / per_round;
@@ -1273,13 +1451,16 @@ __device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot,
 #pragma unroll
                             for (int j = 0; j < 4; ++j) {
                                 if (e0 + lane < l4[j]) {
-                                    F inc;
-                                    if constexpr (Num<F>::is_float) inc = w4[j] * (float)(int)dz4[j];
-                                    else inc = w4[j] * dz4[j];
                                     // a level's only variable: its row's columns are
                                     // distinct and nothing else touches the cache now
-                                    if (solo) cache[col4[j]] += inc;
-                                    else atomic_add_field(cache + col4[j], inc);
+                                    if (solo) {
+                                        solo_add(cache + col4[j], w4[j], dz4[j]);
+                                    } else {
+                                        F inc;
+                                        if constexpr (Num<F>::is_float) inc = w4[j] * (float)(int)dz4[j];
+                                        else inc = w4[j] * dz4[j];
+                                        atomic_add_field(cache + col4[j], inc);
+                                    }
                                 }
                             }
                         }
@@ -1312,10 +1493,7 @@ __device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot,
                     const long long zold = ent[1], znew = ent[2];
                     if constexpr (KIND == KIND_QUIO) {
                         if (solo) {   // one row, distinct columns: no atomics needed
-                            if constexpr (Num<F>::is_float)
-                                cache[m.adj_col[e]] += __ldg(m.adj_f + e) * (float)(int)(znew - zold);
-                            else
-                                cache[m.adj_col[e]] += m.adj_i[e] * (znew - zold);
+                            solo_add(cache + m.adj_col[e], Coef<F>::adj(m, e), znew - zold);
                         } else {
                             quio_update_range<F>(m, cache, e, e + 1, 1, znew - zold);
                         }

@@ -100,6 +100,37 @@ def quio_dense_small(seed: int = 0, n: int = 32, lo: int = -8, hi: int = 7):
     return _pack_arrays(n, np.full(n, lo), np.full(n, hi), offs, flat, coeffs, "i32")
 
 
+def quio_complete(seed: int = 0, n: int = 200, lo: int = -40, hi: int = 40):
+    """Complete-graph integer QUIO (every pair coupled, so every dependency
+    level holds one variable): h ~ U{-20..20}, J_ii ~ U{0..5}, J_ij ~
+    U{-10..-1, 1..10} (i<j, never zero)."""
+    rng = np.random.default_rng(seed)
+    h = rng.integers(-20, 21, size=n)
+    d = rng.integers(0, 6, size=n)
+    iu, ju = np.triu_indices(n, k=1)
+    J = rng.integers(1, 11, size=len(iu)) * rng.choice([-1, 1], size=len(iu))
+    offs, flat, coeffs = _quio_arrays(n, np.arange(n), h, np.arange(n), d, iu, ju, J)
+    return _pack_arrays(n, np.full(n, lo), np.full(n, hi), offs, flat, coeffs, "i32")
+
+
+def quio_chain(seed: int = 0, n: int = 300, lo: int = -8, hi: int = 7, n_long: int = 0):
+    """Integer QUIO on the path 0-1-...-(n-1) (every level one variable, rows
+    of at most two entries), plus n_long random longer-range couplings:
+    h ~ U{-20..20}, J_ii ~ U{0..5}, J_ij ~ U{-10..-1, 1..10}."""
+    rng = np.random.default_rng(seed)
+    h = rng.integers(-20, 21, size=n)
+    d = rng.integers(0, 6, size=n)
+    pairs = {(k, k + 1) for k in range(n - 1)}
+    while len(pairs) < n - 1 + n_long:
+        a, b = sorted(int(x) for x in rng.choice(n, size=2, replace=False))
+        pairs.add((a, b))
+    iu = np.array([a for a, _ in sorted(pairs)], np.int64)
+    ju = np.array([b for _, b in sorted(pairs)], np.int64)
+    J = rng.integers(1, 11, size=len(iu)) * rng.choice([-1, 1], size=len(iu))
+    offs, flat, coeffs = _quio_arrays(n, np.arange(n), h, np.arange(n), d, iu, ju, J)
+    return _pack_arrays(n, np.full(n, lo), np.full(n, hi), offs, flat, coeffs, "i32")
+
+
 def random_graph_edges(rng, n: int, n_edges: int):
     """Distinct undirected edges (i<j) drawn uniformly (Erdos-Renyi G(n, m))."""
     max_edges = n * (n - 1) // 2

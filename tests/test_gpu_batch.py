@@ -111,6 +111,34 @@ def test_batch_float_instances():
         assert stats.ks_2samp(res[i][1], eo).pvalue > 0.01, i
 
 
+@pytest.mark.parametrize("rule", ["metropolis", "heat_bath", "opt_metropolis"])
+def test_batch_speculative_equals_level_order(rule):
+    """A batch mixing complete, nearly complete, path-like and sparse integer
+    instances gives, with speculative windows, the states, energies and change
+    counts of the level-by-level order bit for bit, before and after autotuning."""
+    from paper_2511_17245_gb300 import _lib
+    insts = []
+    for i in range(4):
+        insts.append(wl.quio_complete(20 + i, n=40 + 60 * i, lo=-20, hi=20))
+        insts.append(wl.quio_dense_small(30 + i, n=30 + 40 * i, lo=-8, hi=7))
+        insts.append(wl.quio_chain(40 + i, n=100 + 50 * i, lo=-30, hi=30, n_long=10 * i))
+        insts.append(wl.quio_sparse_int(50 + i, n=150, n_edges=600, lo=-5, hi=5))
+    models = [Model(x) for x in insts]
+    runs = []
+    for flags in (_lib.SA_FLAG_NO_SPECULATION, 0):
+        params = []
+        for i, m in enumerate(models):
+            tmax, tmin = m.default_temperatures()
+            params.append(make_params(rule, 60, 16, seed=1, instance_id=i, t_max=tmax, t_min=tmin, flags=flags))
+        runs.append(_batch_results(models, params)[0])
+        if flags == 0:
+            runs.append(_batch_results(models, params, autotune=3)[0])
+    for got in runs[1:]:
+        for i in range(len(models)):
+            for j in range(3):
+                np.testing.assert_array_equal(runs[0][i][j], got[i][j], err_msg=f"instance {i} output {j}")
+
+
 def test_batch_full_size_sampled():
     """4,096 instances (N log-uniform in [50, 2000], range width log-uniform in
     [2, 1024], half dense / half sparse with degree 8..64), 32 replicas, 1000

@@ -20,6 +20,7 @@ torch = pytest.importorskip("torch")
 
 from oracle import oracle as orc
 from paper_2511_17245_gb300 import Model, make_params, sa_run, sa_run_report, RULES
+from paper_2511_17245_gb300 import _lib
 from paper_2511_17245_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -139,6 +140,62 @@ def test_huio_zipf_full_size_sampled(rule):
     inst = wl.huio_zipf(2)
     S = {"metropolis": 300, "heat_bath": 40, "opt_metropolis": 300}[rule]
     _check_int_parity(inst, rule, S, 256, 0, 2, label="huio-zipf-2000")
+
+
+SPEC_CASES = {
+    # every level one variable, rows of all j != k: the columns are implicit
+    "complete_int": lambda: wl.quio_complete(5, n=200, lo=-40, hi=40),
+    # a few zero couplings: mostly single-variable levels, rows read with columns
+    "dense_int_zeros": lambda: wl.quio_dense_small(6, n=150, lo=-8, hi=7),
+    # path graph plus long-range couplings: single-variable levels, short rows
+    "chain_int": lambda: wl.quio_chain(7, n=400, lo=-30, hi=30, n_long=40),
+    # fp32 complete graph (fields in fp32, energies refreshed in FP64)
+    "complete_float": lambda: wl.batch_instance({"index": 0, "n": 180, "width": 40, "dense": True, "deg": 0,
+                                                 "seed": 11}),
+}
+
+
+@pytest.mark.parametrize("case", sorted(SPEC_CASES))
+@pytest.mark.parametrize("rule", ALL_RULES)
+def test_speculative_windows_equal_level_order(case, rule):
+    """Runs of single-variable levels decided 32 at a time by one warp give the
+    states, energies, change counts, per-attempt traces and per-sweep energies
+    of the level-by-level order, bit for bit, for several launch shapes (float
+    energies: bit for bit at the same thread count)."""
+    model = Model(SPEC_CASES[case]())
+    tmax, tmin = model.default_temperatures()
+    S, R, n = 40, 24, model.n
+    edt = torch.float64 if model.is_float else torch.int64
+
+    def run(**kw):
+        tr = torch.zeros((S, R, n), dtype=torch.int32, device="cuda")
+        et = torch.zeros((S, R), dtype=edt, device="cuda")
+        out = model.run(rule, S, R, seed=2, t_max=tmax, t_min=tmin, trace=tr, trace_replicas=R,
+                        energy_trace=et.data_ptr(), **kw)
+        out["trace"], out["energy_trace"] = tr, et
+        return out
+
+    ref = run(flags=_lib.SA_FLAG_NO_SPECULATION)
+    for extra in [dict(), dict(replicas_per_block=2, threads_per_replica=64),
+                  dict(replicas_per_block=1, threads_per_replica=256), dict(flags=_lib.SA_FLAG_STATE_IN_GLOBAL)]:
+        got = run(**extra)
+        for key in ("states", "accepts", "trace"):
+            assert torch.equal(ref[key], got[key]), (case, rule, extra, key)
+        for key in ("energies", "energy_trace"):
+            if not model.is_float or "threads_per_replica" not in extra:
+                assert torch.equal(ref[key], got[key]), (case, rule, extra, key)
+            else:
+                # FP64 energy partial sums are split over the replica's threads:
+                # another thread count rounds them in another order
+                torch.testing.assert_close(ref[key], got[key], rtol=1e-12, atol=1e-9)
+    # the level-by-level order itself follows the oracle (integer models)
+    if not model.is_float and case != "dense_int_zeros":
+        om = orc.Model(SPEC_CASES[case]())
+        tr = ref["trace"].cpu().numpy()
+        res = _oracle_follow(om, rule, S, 2, tmax, tmin, range(4), tr, R)
+        for r, x in zip(range(4), res):
+            assert x["follow"]["mismatch"] == 0, (case, rule, r, x["follow"])
+            assert np.array_equal(x["states"][0], ref["states"][r].cpu().numpy())
 
 
 def test_state_placement_and_launch_shape_invariance():
@@ -362,7 +419,6 @@ def test_time_sliced_equals_plain_waves(rule):
     which replicas cut between two groups hand their state over, gives the
     plain waves' results bit for bit, and its traced replicas (replica 1 is
     split between groups 0 and 1) replay exactly against the oracle."""
-    from paper_2511_17245_gb300 import _lib
     inst = wl.quio_sparse_int(13, n=10000, n_edges=60000, lo=-30, hi=200, jmax=4, hmax=40, dmax=3)
     model = Model(inst)
     om = orc.Model(inst)
@@ -388,7 +444,6 @@ def test_time_sliced_float_benchmark_shape():
     benchmark's shape: 608 resident groups) runs time-sliced; every replica's
     energy is within 1e-5 of the FP64 recomputation and the energies match the
     plain waves' by a KS test."""
-    from paper_2511_17245_gb300 import _lib
     inst = wl.quio_sparse_wide(1)
     model = Model(inst)
     tmax, tmin = model.default_temperatures()

@@ -57,7 +57,7 @@ def _compile_and_run(tmp_path, body):
 def test_plan_run_shape_benchmark_workload(tmp_path):
     """The 10,000-variable [0,255] fp32 workload (43 levels) with 1024 replicas on
     152 SMs and 227 KB of shared memory per block: 128 threads per replica,
-    51,760 bytes of state each, 4 replicas per block, 256 blocks."""
+    51,856 bytes of state each, 4 replicas per block, 256 blocks."""
     body = """
   sa::PlanModel m{10000, 43, sa::KIND_QUIO, 1, 1, 40, 10000};
   sa::RunPlan p{};
@@ -73,10 +73,10 @@ def test_plan_run_shape_benchmark_workload(tmp_path):
   std::printf("%d\\n", err == nullptr);
 """
     out = _compile_and_run(tmp_path, body)
-    assert out[:12] == ["1", "128", "4", "256", "51760", "207040", "0", "10000", "50000", "50016", "51552", "51584"]
+    assert out[:12] == ["1", "128", "4", "256", "51856", "207424", "0", "10000", "50000", "50112", "51648", "51680"]
     assert out[12:16] == ["1", "1", "4", "0"]          # forced global state: same shape, no shared memory
     assert out[16] == "0"                               # 48 threads: not whole warps
-    assert out[17] == "0"                               # 5 replicas of 51,760 bytes exceed shared memory
+    assert out[17] == "0"                               # 5 replicas of 51,856 bytes exceed shared memory
 
 
 def test_plan_schedule_closed_form(tmp_path):
