@@ -17,8 +17,10 @@ workload on its own GPU (replicas only: no collective on the data path) and
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -47,6 +49,40 @@ def _peaks():
             return json.load(f), "measured"
     except Exception:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def kernel_source_hash():
+    """Hash of the CUDA sources and public headers: identifies the build whose
+    counters a profile summary records."""
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2511_17245_gb300", "csrc")
+    inc = os.path.join(ROOT, "include")
+    files = [os.path.join(csrc, f) for f in sorted(os.listdir(csrc))]
+    files += [os.path.join(inc, f) for f in sorted(os.listdir(inc)) if f.endswith(".h")]
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic(rule, sweeps, replicas):
+    """DRAM bytes (read + write) per launch of the rule's sweep kernel on this
+    workload, from the single-pass ncu capture recorded under profiles/, when
+    that capture was taken of these sources at this size; else (None, reason)."""
+    path = os.path.join(ROOT, "profiles", f"dram_{rule}_quio_sparse_wide.md")
+    if not os.path.exists(path):
+        return None, "no capture recorded"
+    with open(path) as fh:
+        m = re.search(r"traffic: dram_bytes_per_launch=(\d+) sweeps=(\d+) replicas=(\d+) source_hash=(\w+)",
+                      fh.read())
+    if not m:
+        return None, "no capture recorded"
+    if int(m.group(2)) != sweeps or int(m.group(3)) != replicas:
+        return None, "capture taken at another size"
+    if m.group(4) != kernel_source_hash():
+        return None, "sources changed since the capture"
+    return int(m.group(1)), f"ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch ({os.path.basename(path)})"
 
 
 def rule_roofline(rule, ms, attempts, change_rate, width, peaks_dev):
@@ -581,7 +617,7 @@ def main():
         e_re = model.energy(states).double()
         rel = ((energies - e_re).abs() / e_re.abs().clamp_min(1e-300)).max().item()
         reports[rule] = {"threads_per_replica": rep.threads_per_replica, "replicas_per_block": rep.replicas_per_block,
-                         "blocks": rep.blocks, "shared_bytes": rep.shared_bytes,
+                         "blocks": rep.blocks, "shared_bytes": rep.shared_bytes, "time_sliced": rep.time_sliced,
                          "max_refresh_drift": rep.max_refresh_drift,
                          "final_energy_max_rel_err_vs_fp64_recompute": rel}
     for _ in range(max(0, args.warmup - 1)):
@@ -630,8 +666,8 @@ def main():
                                             HI - LO + 1, peaks_dev)
         per_rule[rule]["change_rate"] = change_rates[rule]
     roof = dict(per_rule_roof[dom])
-    roof["kernel"] = f"sweep_kernel<{dom}>"
-    roof["traffic"] = None
+    roof["kernel"] = f"{'sweep_sliced_kernel' if reports[dom]['time_sliced'] else 'sweep_kernel'}<{dom}>"
+    roof["traffic"], roof["traffic_source"] = captured_traffic(dom, S, R)
     roof["limiter"] = ("ncu: latency-bound (few warps per SM: the replica state fills shared memory; "
                        "per-level barriers; dependent decision chains), not the listed ceiling")
     # ---- e2e through the C ABI with host buffers (model upload + host outputs each step)
