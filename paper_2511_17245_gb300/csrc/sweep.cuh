@@ -266,9 +266,12 @@ __device__ long long opt_argmin(const VarView<F, KIND>& vv, long long z, long lo
         if (a2 > F(0)) {
             long long q;
             if constexpr (Num<F>::is_float) {
+                // bounds fit int32 (model compiler), so the clamp and the
+                // conversion back stay in 32-bit conversions (64-bit ones run on
+                // the FP64 pipe); hi + 1 = 2^31 is the one value beyond int32
                 float qv = floorf(-a1 / (2.f * a2));
-                qv = fminf(fmaxf(qv, (float)lo - 1.f), (float)hi + 1.f);
-                q = (long long)qv;
+                qv = fminf(fmaxf(qv, __int2float_rn((int)lo) - 1.f), __int2float_rn((int)hi) + 1.f);
+                q = qv >= 2147483648.f ? 2147483648LL : (long long)__float2int_rz(qv);
             } else {
                 q = floor_div(-a1, 2 * a2);
             }
@@ -789,7 +792,8 @@ __device__ void quio_recompute(const DevModel& m, const Z* zs, F* cache, int t, 
             for (int e = mt.link_begin; e < mt.link_begin + mt.link_len; ++e) {
                 const int j = m.adj_col[e];
                 const double w = m.adj_d ? m.adj_d[e] : (double)m.adj_f[e];
-                f += w * (double)((long long)m.meta[j].lo + (long long)zs[j]);
+                // z_j fits int32 (model compiler): a 32-bit source conversion
+                f += w * __int2double_rn(m.meta[j].lo + (int)zs[j]);
             }
             const float ff = (float)f;
             if (measure) drift = fmaxf(drift, (float)fabs((double)cache[k] - f));
