@@ -322,6 +322,65 @@ def test_heat_bath_closed_form_multilinear():
 
 
 # ----------------------------------------------------------------- runs
+def _sweep_params(n_sweeps, s, t_max, t_min):
+    frac = s / (n_sweeps - 1) if n_sweeps > 1 else 0.0
+    T = t_max * (t_min / t_max) ** frac
+    beta = np.float32(1.0 / T)
+    ratio = np.float32(s) / np.float32(n_sweeps - 1) if n_sweeps > 1 else np.float32(0)
+    return beta, ratio
+
+
+def _python_attempt(inst, rule, z, k, s, beta, ratio, key, replica):
+    """One attempt of Sect. 3.3 on variable k of state z (full-energy
+    recomputation for every candidate); returns (new value, near-threshold)."""
+    lo, hi = inst["lower"], inst["upper"]
+    width = int(hi[k] - lo[k])
+    if width == 0:
+        return z[k], False
+    w = [int(x) for x in orc.philox4x32_10([k, s, replica, 0], key)]
+    e0 = _raw_energy(inst, z)
+
+    def dE(v):
+        z2 = list(z)
+        z2[k] = v
+        return _raw_energy(inst, z2) - e0
+
+    if rule == "heat_bath":
+        vals = list(range(int(lo[k]), int(hi[k]) + 1))
+        des = [dE(v) for v in vals]
+        mn = min(des)
+        ws = [float(np.exp(-(np.float32(d - mn) * beta), dtype=np.float32)) for d in des]
+        thr = ((w[0] >> 8) + 1) * 2.0 ** -24 * sum(ws)
+        c = 0.0
+        for v, wt in zip(vals, ws):
+            c += wt
+            if c >= thr:
+                return v, False
+        return vals[-1], False
+    if rule == "opt_metropolis" and np.float32((w[2] >> 8) * 2.0 ** -24) < ratio:
+        cands = [v for v in range(int(lo[k]), int(hi[k]) + 1) if v != z[k]]
+        prop = min(cands, key=lambda v: (dE(v), v))
+    else:
+        j = (w[0] * width) >> 32
+        off = z[k] - int(lo[k])
+        prop = int(lo[k]) + (j + 1 if j >= off else j)
+    d = dE(prop)
+    if d <= 0:
+        return prop, False
+    p = float(np.exp(-(np.float32(d) * beta), dtype=np.float32))
+    U = (w[1] >> 8) * 2.0 ** -24
+    return (prop if U < p else z[k]), abs(U - p) <= 1e-6 * p
+
+
+def _python_init(inst, key, replica):
+    lo, hi = inst["lower"], inst["upper"]
+    z = []
+    for k in range(inst["n_vars"]):
+        w = orc.philox4x32_10([k, 0xFFFFFFFF, replica, 0], key)
+        z.append(int(lo[k]) + ((int(w[0]) * int(hi[k] - lo[k] + 1)) >> 32))
+    return z
+
+
 def _python_sa(inst, rule, n_sweeps, seed, t_max, t_min, replica):
     """Independent plain-Python SA of Sect. 3 on a tiny instance: full-energy
     recomputation for every candidate, paper's rules, the documented random
@@ -330,70 +389,62 @@ def _python_sa(inst, rule, n_sweeps, seed, t_max, t_min, replica):
     value of z_k after every attempt ([S][N])."""
     n = inst["n_vars"]
     trace = np.zeros((n_sweeps, n), np.int32)
-    lo, hi = inst["lower"], inst["upper"]
     key = [seed & 0xFFFFFFFF, seed >> 32]
-
-    def E(z):
-        return _raw_energy(inst, z)
-
-    z = []
-    for k in range(n):
-        w = orc.philox4x32_10([k, 0xFFFFFFFF, replica, 0], key)
-        z.append(int(lo[k]) + ((int(w[0]) * int(hi[k] - lo[k] + 1)) >> 32))
+    z = _python_init(inst, key, replica)
     near = 0
     for s in range(n_sweeps):
-        frac = s / (n_sweeps - 1) if n_sweeps > 1 else 0.0
-        T = t_max * (t_min / t_max) ** frac
-        beta = np.float32(1.0 / T)
-        ratio = np.float32(s) / np.float32(n_sweeps - 1) if n_sweeps > 1 else np.float32(0)
+        beta, ratio = _sweep_params(n_sweeps, s, t_max, t_min)
         for k in range(n):
-            width = int(hi[k] - lo[k])
-            if width == 0:
-                continue
-            w = [int(x) for x in orc.philox4x32_10([k, s, replica, 0], key)]
-            e0 = E(z)
-
-            def dE(v):
-                z2 = list(z)
-                z2[k] = v
-                return E(z2) - e0
-
-            if rule == "heat_bath":
-                vals = list(range(int(lo[k]), int(hi[k]) + 1))
-                des = [dE(v) for v in vals]
-                mn = min(des)
-                ws = [float(np.exp(-(np.float32(d - mn) * beta), dtype=np.float32)) for d in des]
-                thr = ((w[0] >> 8) + 1) * 2.0 ** -24 * sum(ws)
-                c = 0.0
-                pick = vals[-1]
-                for v, wt in zip(vals, ws):
-                    c += wt
-                    if c >= thr:
-                        pick = v
-                        break
-                z[k] = pick
-                trace[s, k] = z[k]
-                continue
-            if rule == "opt_metropolis" and np.float32((w[2] >> 8) * 2.0 ** -24) < ratio:
-                cands = [v for v in range(int(lo[k]), int(hi[k]) + 1) if v != z[k]]
-                prop = min(cands, key=lambda v: (dE(v), v))
-            else:
-                j = (w[0] * width) >> 32
-                off = z[k] - int(lo[k])
-                prop = int(lo[k]) + (j + 1 if j >= off else j)
-            d = dE(prop)
-            if d <= 0:
-                z[k] = prop
-                trace[s, k] = z[k]
-                continue
-            p = float(np.exp(-(np.float32(d) * beta), dtype=np.float32))
-            U = (w[1] >> 8) * 2.0 ** -24
-            if abs(U - p) <= 1e-6 * p:
-                near += 1
-            if U < p:
-                z[k] = prop
+            z[k], nt = _python_attempt(inst, rule, z, k, s, beta, ratio, key, replica)
+            near += nt
             trace[s, k] = z[k]
     return np.array(z), near, trace
+
+
+@pytest.mark.parametrize("rule", ["metropolis", "heat_bath", "opt_metropolis"])
+@pytest.mark.parametrize("window", [2, 5, 32])
+def test_speculative_windows_reproduce_sequential_order(rule, window):
+    """On a complete graph (every variable depends on every earlier one), the
+    attempts of up to `window` consecutive variables decided from the same
+    state, kept up to and including the first one that changes its variable,
+    give the sequential trajectory of Sect. 3.1 attempt by attempt."""
+    inst = wl.quio_complete(9, n=9, lo=-3, hi=3)
+    n, S, seed = inst["n_vars"], 6, 0x77
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for rep in range(2):
+        ref = _python_sa(inst, rule, S, seed, 40.0, 0.5, rep)[2]
+        z = _python_init(inst, key, rep)
+        got = np.zeros((S, n), np.int32)
+        windows = changes = 0
+        for s in range(S):
+            beta, ratio = _sweep_params(S, s, 40.0, 0.5)
+            i = 0
+            while i < n:
+                snap = list(z)
+                dec = [_python_attempt(inst, rule, snap, k, s, beta, ratio, key, rep)[0]
+                       for k in range(i, min(i + window, n))]
+                p = next((q for q, v in enumerate(dec) if v != snap[i + q]), len(dec))
+                done = min(p + 1, len(dec))   # decisions kept: up to the first change
+                for q in range(done):
+                    z[i + q] = dec[q]
+                    got[s, i + q] = dec[q]
+                windows += 1
+                changes += p < len(dec)
+                i += done
+        assert np.array_equal(got, ref), (rule, window, rep)
+        assert windows > changes > 0
+    # a planted mistake (keeping the decision after the first change) is caught
+    if window > 2 and rule == "metropolis":
+        z = _python_init(inst, key, 0)
+        ref = _python_sa(inst, rule, S, seed, 40.0, 0.5, 0)[2]
+        bad = np.zeros((S, n), np.int32)
+        for s in range(S):
+            beta, ratio = _sweep_params(S, s, 40.0, 0.5)
+            snap = list(z)
+            for k in range(n):
+                z[k] = _python_attempt(inst, rule, snap, k, s, beta, ratio, key, 0)[0]
+                bad[s, k] = z[k]
+        assert not np.array_equal(bad, ref)
 
 
 @pytest.mark.parametrize("rule", ["metropolis", "heat_bath", "opt_metropolis"])
