@@ -174,6 +174,11 @@ typedef struct {
     void* energy_trace;           /* optional device int64 (integer models) or double
                                      (float models) [S][R]: energy after every sweep     */
     sa_run_report* report;        /* optional host report                                */
+    int32_t* best_states;         /* optional int32[R][N] (host or device): per replica, the
+                                     lowest-energy state at the end of any sweep (with
+                                     best_energies; see sa_run)                          */
+    void* best_energies;          /* optional int64[R] (integer models) or double[R] (float
+                                     models), host or device: the energy of best_states  */
 } sa_run_params;
 
 /*
@@ -192,6 +197,16 @@ typedef struct {
  *                 FP64 recomputation from the final state for float models).
  *   out_accepts   optional uint64[R] (host or device): number of attempts that
  *                 changed the variable.
+ *
+ * Best-state tracking (params->best_states and params->best_energies, both
+ * or neither): among the states at the ends of sweeps 0..S-1, the one with the
+ * lowest tracked energy, the earliest on ties (the final state is a
+ * candidate, so the best energy never exceeds the final one).  The tracked
+ * energy is exact for integer models; for float models it is the fp32-updated
+ * energy, exact in FP64 at refresh sweeps, and best_energies holds the FP64
+ * recomputation of the chosen state.  Cost: one group reduction per sweep and
+ * N int32 stores per sweep that improves on the best so far.  Not available in
+ * batches, served requests and sa_run_noalloc (SA_ERR_UNSUPPORTED there).
  *
  * Visiting order: within a sweep variables are updated in index order
  * (Sect. 3.1).  The kernels run the updates of variables that share no term
@@ -248,9 +263,10 @@ sa_status sa_energy(const sa_model* model, const int32_t* states, int64_t n_stat
  *                  coefficient class (integer or float), and all params one rule
  *                  (SA_ERR_UNSUPPORTED otherwise).  n_sweeps, n_replicas, seed,
  *                  instance_id, temperatures and init_states (device memory) may
- *                  differ per instance; trace must be NULL.  The batch owns its
- *                  device buffers (arguments, schedules, outputs) and a CUDA
- *                  graph holding the launch.  Synchronous.
+ *                  differ per instance; trace, best_states and best_energies must
+ *                  be NULL.  The batch owns its device buffers (arguments,
+ *                  schedules, outputs) and a CUDA graph holding the launch.
+ *                  Synchronous.
  * sa_batch_autotune  times the launch with threads_per_replica in
  *                  {32, 64, 96, 128, 256} (replicas per block: as many as shared
  *                  memory holds) on a run truncated to trial_sweeps sweeps on
@@ -308,7 +324,8 @@ void sa_batch_destroy(sa_batch* batch);
  *                   the thread-group size of the serving kernel (two groups
  *                   of 256 per SM, each with a ~112 KB state region, by default).
  * sa_server_submit  copies params (and params->temperatures); trace,
- *                   energy_trace, report and init_states must be NULL.  The model
+ *                   energy_trace, report, init_states, best_states and
+ *                   best_energies must be NULL.  The model
  *                   must stay alive until the request is finished.  A request
  *                   larger than the whole budget fails with SA_ERR_OOM.
  * sa_server_poll    state: SA_REQ_QUEUED, _RUNNING, _DONE, _FAILED, _CANCELLED.
@@ -364,7 +381,8 @@ void sa_server_destroy(sa_server* server);
  *
  * Arguments and results are those of sa_run, with these differences:
  *   - out_states, out_energies, out_accepts and params->init_states must be
- *     device pointers (SA_ERR_INVALID otherwise); params->report must be NULL.
+ *     device pointers (SA_ERR_INVALID otherwise); params->report must be NULL;
+ *     best-state tracking is not available (SA_ERR_UNSUPPORTED).
  *   - The run's scratch (the per-sweep temperature table, and the replicas'
  *     state when it does not fit in shared memory) lives in one fixed device
  *     array of SA_NOALLOC_SCRATCH_BYTES bytes compiled into the library; every

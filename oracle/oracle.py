@@ -80,7 +80,7 @@ def _load():
         lib.om_auto_temperatures.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         lib.om_run.argtypes = [P, C.c_int, C.c_int32, C.c_uint64, C.c_uint32, C.c_double, C.c_double,
                                C.c_double, C.c_int32, C.c_int32, P, P, C.c_int32, P, P, P, P, P, P,
-                               C.POINTER(FollowStats), P, P, P]
+                               C.POINTER(FollowStats), P, P, P, P, P, P]
         lib.om_run.restype = C.c_int
         lib.om_attempt.argtypes = [P, P, C.c_int32, C.c_int, C.c_float, C.c_float, C.c_uint64,
                                    C.c_uint32, C.c_uint32, C.c_uint32]
@@ -184,7 +184,7 @@ class Model:
 
     def run(self, rule, n_sweeps, seed, t_max, t_min, r_begin=0, r_end=1, instance=0,
             init_states=None, trace=None, trace_replicas=0, margin=1e-6, energy_trace=False,
-            record_trace=False):
+            record_trace=False, best=False):
         """SA run for replicas [r_begin, r_end); see om_run in sa_oracle.c."""
         R = r_end - r_begin
         out_z = np.zeros((R, self.n), np.int32)
@@ -199,16 +199,22 @@ class Model:
         et_i = np.zeros((n_sweeps, R), np.int64) if energy_trace else None
         et_f = np.zeros((n_sweeps, R), np.float64) if energy_trace else None
         tr_out = np.zeros((n_sweeps, R, self.n), np.int32) if record_trace else None
+        b_z = np.zeros((R, self.n), np.int32) if best else None
+        b_i = np.zeros(R, np.int64) if best else None
+        b_f = np.zeros(R, np.float64) if best else None
         rc = self._lib.om_run(self._h, RULES[rule] if isinstance(rule, str) else int(rule), int(n_sweeps),
                               C.c_uint64(seed), C.c_uint32(instance), float(t_max), float(t_min), float(margin),
                               int(r_begin), int(r_end), _ptr(init), _ptr(tr), int(trace_replicas),
                               _ptr(out_z), _ptr(e_i), _ptr(e_f), _ptr(er_i), _ptr(er_f), _ptr(ch),
-                              C.byref(st), _ptr(et_i), _ptr(et_f), _ptr(tr_out))
+                              C.byref(st), _ptr(et_i), _ptr(et_f), _ptr(tr_out), _ptr(b_z), _ptr(b_i), _ptr(b_f))
         if rc != 0:
             raise ValueError(f"oracle run rejected (code {rc})")
         res = {"states": out_z, "changes": ch, "follow": st.as_dict()}
         if record_trace:
             res["trace"] = tr_out
+        if best:
+            res["best_states"] = b_z
+            res["best_energy"] = b_f if self.is_float else b_i
         if self.is_float:
             res["energy"] = e_f
             res["energy_recomputed"] = er_f

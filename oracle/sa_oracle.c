@@ -580,7 +580,10 @@ static attempt_out attempt(const om_model *m, const int32_t *z, int32_t k, uint6
 /* (indexed by absolute replica number).  trace_out (optional) receives this  */
 /* run's own values in the layout [S][r_end - r_begin][N].                    */
 /* Outputs per replica (indexed from r_begin): final z [R x N], tracked E,   */
-/* recomputed E, number of changes.                                           */
+/* recomputed E, number of changes.  Optional best state (best_z, R x N):    */
+/* among the states after sweeps 0..S-1 the first with the lowest tracked E  */
+/* (the paper is silent on it; it names the optimal solution as the goal,    */
+/* Sect. 2), with its recomputed E in best_e_i / best_e_f.                   */
 /* ------------------------------------------------------------------------ */
 int om_run(const om_model *m, int rule, int32_t n_sweeps, uint64_t seed, uint32_t inst,
            double t_max, double t_min, double margin,
@@ -589,7 +592,8 @@ int om_run(const om_model *m, int rule, int32_t n_sweeps, uint64_t seed, uint32_
            int32_t *out_z, int64_t *out_e_i, double *out_e_f,
            int64_t *out_e_recomputed_i, double *out_e_recomputed_f,
            int64_t *out_changes, om_follow_stats *stats,
-           int64_t *energy_trace_i, double *energy_trace_f, int32_t *trace_out)
+           int64_t *energy_trace_i, double *energy_trace_f, int32_t *trace_out,
+           int32_t *best_z, int64_t *best_e_i, double *best_e_f)
 {
     if (rule < 0 || rule > 2 || n_sweeps < 1 || r_end < r_begin) return OM_ERR_INVALID;
     int32_t n = m->n;
@@ -617,6 +621,11 @@ int om_run(const om_model *m, int rule, int32_t n_sweeps, uint64_t seed, uint32_
         double e_f = m->is_float ? om_energy_f(m, z) : 0.0;
         int64_t changes = 0;
         int follow = (trace != NULL) && (r < trace_replicas);
+        /* best state at sweep ends: strictly lower tracked energy replaces it */
+        int have_best = 0;
+        int64_t bst_i = 0;
+        double bst_f = 0.0;
+        int32_t *bz = best_z ? best_z + (int64_t)(r - r_begin) * n : NULL;
         for (int32_t s = 0; s < n_sweeps; ++s) {
             attempt_ctx cx = {rule, beta[s], ratio[s], margin};
             for (int32_t k = 0; k < n; ++k) {
@@ -633,8 +642,16 @@ int om_run(const om_model *m, int rule, int32_t n_sweeps, uint64_t seed, uint32_
             }
             if (energy_trace_i) energy_trace_i[(int64_t)s * (r_end - r_begin) + (r - r_begin)] = e_i;
             if (energy_trace_f) energy_trace_f[(int64_t)s * (r_end - r_begin) + (r - r_begin)] = e_f;
+            if (bz && (!have_best || (m->is_float ? e_f < bst_f : e_i < bst_i))) {
+                have_best = 1;
+                bst_i = e_i;
+                bst_f = e_f;
+                memcpy(bz, z, sizeof(int32_t) * n);
+            }
         }
         int64_t idx = r - r_begin;
+        if (bz && best_e_i) best_e_i[idx] = m->is_float ? 0 : om_energy_i(m, bz);
+        if (bz && best_e_f) best_e_f[idx] = m->is_float ? om_energy_f(m, bz) : (double)om_energy_i(m, bz);
         if (out_e_i) out_e_i[idx] = e_i;
         if (out_e_f) out_e_f[idx] = e_f;
         if (out_e_recomputed_i) out_e_recomputed_i[idx] = m->is_float ? 0 : om_energy_i(m, z);

@@ -52,18 +52,25 @@ class Model:
         return sa_default_temperatures(self.handle)
 
     def run(self, rule="metropolis", n_sweeps=1000, n_replicas=64, seed=0, device="cuda", stream=None,
-            report=False, **kw):
-        """Runs sa_run into freshly allocated torch tensors; returns a dict."""
+            report=False, best=False, **kw):
+        """Runs sa_run into freshly allocated torch tensors; returns a dict
+        (with best=True also the best states at sweep ends and their energies)."""
         import torch
+        edt = torch.float64 if self.is_float else torch.int64
         states = torch.empty((n_replicas, self.n), dtype=torch.int32, device=device)
-        energies = torch.empty(n_replicas, dtype=torch.float64 if self.is_float else torch.int64, device=device)
+        energies = torch.empty(n_replicas, dtype=edt, device=device)
         accepts = torch.empty(n_replicas, dtype=torch.int64, device=device)
+        if best:
+            kw["best_states"] = torch.empty((n_replicas, self.n), dtype=torch.int32, device=device)
+            kw["best_energies"] = torch.empty(n_replicas, dtype=edt, device=device)
         rep = sa_run_report() if report else None
         params = make_params(rule=rule, n_sweeps=n_sweeps, n_replicas=n_replicas, seed=seed, report=rep, **kw)
         if stream is None and str(device).startswith("cuda"):
             stream = torch.cuda.current_stream().cuda_stream
         sa_run(self.handle, params, states, energies, accepts, stream)
         out = {"states": states, "energies": energies, "accepts": accepts}
+        if best:
+            out["best_states"], out["best_energies"] = kw["best_states"], kw["best_energies"]
         if rep is not None:
             out["report"] = {f: getattr(rep, f) for f, _ in rep._fields_}
         return out

@@ -79,7 +79,7 @@ class sa_run_params(C.Structure):
                 ("instance_id", C.c_uint32), ("replicas_per_block", C.c_int32),
                 ("threads_per_replica", C.c_int32), ("flags", C.c_int32), ("trace", C.c_void_p),
                 ("trace_replicas", C.c_int32), ("_pad0", C.c_int32), ("energy_trace", C.c_void_p),
-                ("report", C.POINTER(sa_run_report))]
+                ("report", C.POINTER(sa_run_report)), ("best_states", C.c_void_p), ("best_energies", C.c_void_p)]
 
 
 # Every symbol include/*.h declares (checked by the tests).
@@ -221,7 +221,7 @@ def sa_default_temperatures(h):
 def make_params(rule="metropolis", n_sweeps=1000, n_replicas=64, seed=0, t_max=0.0, t_min=0.0,
                 temperatures=None, init_states=None, refresh_interval=0, instance_id=0,
                 replicas_per_block=0, threads_per_replica=0, flags=0, trace=None, trace_replicas=0,
-                energy_trace=None, report=None):
+                energy_trace=None, report=None, best_states=None, best_energies=None):
     p = sa_run_params()
     p.rule = RULES[rule] if isinstance(rule, str) else int(rule)
     p.n_sweeps = int(n_sweeps)
@@ -240,6 +240,8 @@ def make_params(rule="metropolis", n_sweeps=1000, n_replicas=64, seed=0, t_max=0
     p.trace_replicas = int(trace_replicas)
     p.energy_trace = ptr(energy_trace)
     p.report = C.pointer(report) if report is not None else None
+    p.best_states = ptr(best_states)
+    p.best_energies = ptr(best_energies)
     return p
 
 

@@ -797,11 +797,14 @@ sa_status sa_run(const sa_model* M, const sa_run_params* p, int32_t* out_states,
         return fail(SA_ERR_INVALID, "trace_replicas out of range");
     if (p->rule == SA_OPT_METROPOLIS && M->max_exp > 4)
         return fail(SA_ERR_UNSUPPORTED, "optimal-transition Metropolis needs exponents <= 4");
+    if ((p->best_states == nullptr) != (p->best_energies == nullptr))
+        return fail(SA_ERR_INVALID, "best_states and best_energies are given together");
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev != M->device) return fail(SA_ERR_INVALID, "model belongs to another device");
     cudaStream_t st = (cudaStream_t)stream;
     const int32_t S = p->n_sweeps, R = p->n_replicas, n = M->n;
+    const bool want_best = p->best_states != nullptr;
 
     // ---- schedule (Sect. 3.1) and OTM ratio (Sect. 3.3.3)
     std::vector<float> tab(2 * (size_t)S);
@@ -828,7 +831,9 @@ sa_status sa_run(const sa_model* M, const sa_run_params* p, int32_t* out_states,
     const bool states_dev = is_device_ptr(out_states);
     const bool en_dev = is_device_ptr(out_energies);
     const bool acc_dev = out_accepts == nullptr || is_device_ptr(out_accepts);
-    const bool sync_needed = !states_dev || !en_dev || !acc_dev || p->report != nullptr;
+    const bool bst_dev = !want_best || is_device_ptr(p->best_states);
+    const bool ben_dev = !want_best || is_device_ptr(p->best_energies);
+    const bool sync_needed = !states_dev || !en_dev || !acc_dev || !bst_dev || !ben_dev || p->report != nullptr;
     float* d_tab = nullptr;
     if ((e = tmp.alloc((void**)&d_tab, tab.size() * sizeof(float))) != cudaSuccess) return cuda_fail(e, "alloc schedule");
     if ((e = cudaMemcpyAsync(d_tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice, st)) != cudaSuccess)
@@ -839,6 +844,10 @@ sa_status sa_run(const sa_model* M, const sa_run_params* p, int32_t* out_states,
     if (!states_dev && (e = tmp.alloc((void**)&d_states, (size_t)R * n * 4)) != cudaSuccess) return cuda_fail(e, "alloc states");
     if (!en_dev && (e = tmp.alloc(&d_en, (size_t)R * 8)) != cudaSuccess) return cuda_fail(e, "alloc energies");
     if (!acc_dev && (e = tmp.alloc((void**)&d_acc, (size_t)R * 8)) != cudaSuccess) return cuda_fail(e, "alloc accepts");
+    int32_t* d_bst = p->best_states;
+    void* d_ben = p->best_energies;
+    if (!bst_dev && (e = tmp.alloc((void**)&d_bst, (size_t)R * n * 4)) != cudaSuccess) return cuda_fail(e, "alloc best states");
+    if (!ben_dev && (e = tmp.alloc(&d_ben, (size_t)R * 8)) != cudaSuccess) return cuda_fail(e, "alloc best energies");
     const int32_t* d_init = p->init_states;
     if (p->init_states && !is_device_ptr(p->init_states)) {
         int32_t* di = nullptr;
@@ -873,6 +882,8 @@ sa_status sa_run(const sa_model* M, const sa_run_params* p, int32_t* out_states,
     a.trace = p->trace;
     a.trace_R = p->trace ? p->trace_replicas : 0;
     a.energy_trace = p->energy_trace;
+    a.best_states = d_bst;
+    a.best_energies = d_ben;
     a.drift_bits = d_drift;
     a.gstate = gstate;
     sa::plan_apply(plan, a);
@@ -924,6 +935,18 @@ sa_status sa_run(const sa_model* M, const sa_run_params* p, int32_t* out_states,
     if (grid_sliced == 0) le = sa::launch_sweep(a, M->zbytes, p->rule, !in_global, blocks, rpc * tpr, shared, stream);
     if (le != 0) return cuda_fail((cudaError_t)le, "sweep launch");
     if (p->report) cudaEventRecord(ev1, st);
+    if (want_best && M->is_float) {
+        // the chosen states' energies in FP64 (the kernel chose by the tracked energy)
+        int32_t* d_bad = nullptr;
+        if ((e = tmp.alloc((void**)&d_bad, 16)) != cudaSuccess) return cuda_fail(e, "alloc flag");
+        cudaMemsetAsync(d_bad, 0, 16, st);
+        sa::EnergyArgs ea{M->dm, d_bst, R, d_ben, d_bad};
+        if ((le = sa::launch_energy(ea, stream)) != 0) return cuda_fail((cudaError_t)le, "energy launch");
+    }
+    if (!bst_dev && (e = cudaMemcpyAsync(p->best_states, d_bst, (size_t)R * n * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(e, "copy best states");
+    if (!ben_dev && (e = cudaMemcpyAsync(p->best_energies, d_ben, (size_t)R * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(e, "copy best energies");
 
     if (!states_dev && (e = cudaMemcpyAsync(out_states, d_states, (size_t)R * n * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_fail(e, "copy states");

@@ -204,6 +204,7 @@ sa_status sa_batch_create(sa_batch** out, const sa_model* const* models, int32_t
         else if (p.rule == SA_OPT_METROPOLIS && v.max_exp > 4) { st = SA_ERR_UNSUPPORTED; msg = "OTM needs exponents <= 4"; }
         else if (p.init_states && !dev_ptr(p.init_states)) { st = SA_ERR_INVALID; msg = "init_states must be device memory"; }
         else if (p.trace) { st = SA_ERR_UNSUPPORTED; msg = "per-attempt traces are not available in batches"; }
+        else if (p.best_states || p.best_energies) { st = SA_ERR_UNSUPPORTED; msg = "best-state tracking is not available in batches"; }
         if (st != SA_OK) {
             delete b;
             return bfail(st, msg + where);

@@ -76,6 +76,8 @@ extern "C" sa_status sa_run_noalloc(const sa_model* M, const sa_run_params* p, i
     if (p->rule < 0 || p->rule > 2) return fail(SA_ERR_INVALID, "unknown rule");
     if (p->n_sweeps < 1 || p->n_replicas < 1) return fail(SA_ERR_INVALID, "n_sweeps and n_replicas must be positive");
     if (p->report) return fail(SA_ERR_INVALID, "sa_run_noalloc does not fill a report");
+    if (p->best_states || p->best_energies)
+        return fail(SA_ERR_UNSUPPORTED, "best-state tracking is not available in sa_run_noalloc");
     if (p->trace && (p->trace_replicas < 0 || p->trace_replicas > p->n_replicas))
         return fail(SA_ERR_INVALID, "trace_replicas out of range");
     if (p->rule == SA_OPT_METROPOLIS && mv.max_exp > 4)

@@ -125,6 +125,8 @@ struct SweepArgs {
     int64_t handoff_bytes;      // bytes of one region: off_ctl + 24 per thread, rounded to 16
     unsigned int* status;       // [0] bit 0: a handoff wait gave up (that replica's outputs are not
                                 // written); [1]: task counter
+    int32_t* best_states;       // [R][N] or null: lowest-energy state at a sweep end
+    void* best_energies;        // [R] (int64 or double): its tracked energy
 };
 
 // One unit of batched work: one replica of one instance.

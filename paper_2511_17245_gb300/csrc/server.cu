@@ -440,8 +440,9 @@ sa_status sa_server_submit(sa_server* s, const sa_model* model, const sa_run_par
     if (v.device != s->device) return sfail(SA_ERR_INVALID, "model belongs to another device than the server");
     if (params->n_sweeps < 1 || params->n_replicas < 1 || params->rule < 0 || params->rule > 2)
         return sfail(SA_ERR_INVALID, "bad run parameters");
-    if (params->trace || params->energy_trace || params->report || params->init_states)
-        return sfail(SA_ERR_UNSUPPORTED, "served requests take no traces, report or initial states");
+    if (params->trace || params->energy_trace || params->report || params->init_states || params->best_states ||
+        params->best_energies)
+        return sfail(SA_ERR_UNSUPPORTED, "served requests take no traces, report, initial or best states");
     if (params->rule == SA_OPT_METROPOLIS && v.max_exp > 4)
         return sfail(SA_ERR_UNSUPPORTED, "OTM needs exponents <= 4");
     if (params->n_replicas > (int32_t)kRingCap) return sfail(SA_ERR_UNSUPPORTED, "too many replicas for the work queue");

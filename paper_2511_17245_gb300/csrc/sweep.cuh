@@ -1094,6 +1094,27 @@ __device__ T group_sum(T v, T* red, int t, int tpr, int bar_id) {
     return tot;
 }
 
+// ------------------------------------------------------------------ best state
+// Optional best state at sweep ends, called by every thread of the group with
+// the sweep's energy `tot` (the same in every thread): the best energy so far
+// lives in the output, where the previous sweep, or the group that ran the
+// replica's earlier sweeps, left it (`first`: this run has none yet).  A
+// strictly lower energy replaces it and the state is copied, so the earliest
+// sweep wins ties.  Kept out of line: it runs only when the caller asks for
+// best states.
+template <class Acc, class Z>
+__device__ __noinline__ void keep_best(const SweepArgs& a, const Z* zs, int r, int t, int tpr, int bar_id, Acc tot,
+                                       bool first) {
+    Acc* bst = reinterpret_cast<Acc*>(a.best_energies) + r;
+    const bool better = first || tot < __ldcg(bst);
+    named_bar(bar_id, tpr);   // every thread has read the old value before thread 0 replaces it
+    if (!better) return;
+    if (t == 0) *bst = tot;
+    int32_t* dst = a.best_states + (size_t)r * a.m.n;
+    for (int k = t; k < a.m.n; k += tpr) dst[k] = (int32_t)((long long)a.m.meta[k].lo + (long long)zs[k]);
+    named_bar(bar_id, tpr);   // every thread has read zs before the next sweep changes it
+}
+
 // ------------------------------------------------------------------ one replica
 // Sweeps [s0, s1) of the SA run of replica r (Sect. 3.1) by the `tpr` threads
 // of one group; `base` is the group's state region (shared or global memory).
@@ -1528,9 +1549,11 @@ __device__ __forceinline__ void replica_body(const SweepArgs& a, const int slot,
                 if (t == 0) eacc += m.const_d;
             }
         }
-        if (a.energy_trace != nullptr) {
-            const Acc tot = group_sum<Acc>(eacc, red, t, tpr, bar_id);
-            if (t == 0) reinterpret_cast<Acc*>(a.energy_trace)[(size_t)s * a.R + r] = tot;
+        if (a.energy_trace != nullptr || a.best_states != nullptr) {
+            const Acc tot = group_sum<Acc>(eacc, red, t, tpr, bar_id);   // the same in every thread
+            if (a.energy_trace != nullptr && t == 0) reinterpret_cast<Acc*>(a.energy_trace)[(size_t)s * a.R + r] = tot;
+            if (a.best_states != nullptr)
+                keep_best<Acc, Z>(a, zs, r, t, tpr, bar_id, tot, s == s0 && restore == nullptr);
         }
     }
 

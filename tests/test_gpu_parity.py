@@ -43,10 +43,10 @@ def _device_run(model, rule, S, R, seed, tmax, tmin, trace_R=0, **kw):
 WORKERS = max(4, os.cpu_count() or 4)
 
 
-def _oracle_follow(om, rule, S, seed, tmax, tmin, replicas, trace, trace_R, workers=WORKERS):
+def _oracle_follow(om, rule, S, seed, tmax, tmin, replicas, trace, trace_R, workers=WORKERS, best=False):
     def one(r):
         return om.run(rule, S, seed, tmax, tmin, r_begin=r, r_end=r + 1, trace=trace, trace_replicas=trace_R,
-                      margin=MARGIN)
+                      margin=MARGIN, best=best)
     with cf.ThreadPoolExecutor(max_workers=workers) as ex:
         return list(ex.map(one, replicas))
 
@@ -425,18 +425,24 @@ def test_time_sliced_equals_plain_waves(rule):
     tmax, tmin = om.auto_temperatures()
     S, R, TR = 30, 400, 4
     trace = torch.zeros((S, TR, model.n), dtype=torch.int32, device="cuda")
-    sliced = model.run(rule, S, R, seed=4, t_max=tmax, t_min=tmin, trace=trace, trace_replicas=TR, report=True)
-    plain = model.run(rule, S, R, seed=4, t_max=tmax, t_min=tmin, flags=_lib.SA_FLAG_NO_TIME_SLICING, report=True)
+    sliced = model.run(rule, S, R, seed=4, t_max=tmax, t_min=tmin, trace=trace, trace_replicas=TR, report=True,
+                       best=True)
+    plain = model.run(rule, S, R, seed=4, t_max=tmax, t_min=tmin, flags=_lib.SA_FLAG_NO_TIME_SLICING, report=True,
+                      best=True)
     torch.cuda.synchronize()
     assert sliced["report"]["time_sliced"] == 1 and plain["report"]["time_sliced"] == 0, sliced["report"]
-    for key in ("states", "energies", "accepts"):
+    for key in ("states", "energies", "accepts", "best_states", "best_energies"):
         assert torch.equal(sliced[key], plain[key]), key
-    res = _oracle_follow(om, rule, S, 4, tmax, tmin, list(range(TR)), trace.cpu().numpy(), TR)
+    res = _oracle_follow(om, rule, S, 4, tmax, tmin, list(range(TR)), trace.cpu().numpy(), TR, best=True)
     st = sliced["states"].cpu().numpy()
     en = sliced["energies"].cpu().numpy()
+    bst = sliced["best_states"].cpu().numpy()
+    ben = sliced["best_energies"].cpu().numpy()
     for r, x in enumerate(res):
         assert x["follow"]["mismatch"] == 0, (rule, r, x["follow"])
         assert np.array_equal(x["states"][0], st[r]) and x["energy"][0] == en[r]
+        # the best state at sweep ends survives the handoffs between groups
+        assert np.array_equal(x["best_states"][0], bst[r]) and x["best_energy"][0] == ben[r]
 
 
 def test_time_sliced_float_benchmark_shape():
@@ -455,3 +461,100 @@ def test_time_sliced_float_benchmark_shape():
     e = out["sliced"]["energies"].cpu().numpy()
     np.testing.assert_allclose(e, model.energy(out["sliced"]["states"]).cpu().numpy(), rtol=1e-5)
     assert stats.ks_2samp(e, out["plain"]["energies"].cpu().numpy()).pvalue > 0.01
+
+
+@pytest.mark.parametrize("rule", ALL_RULES)
+def test_speculative_windows_time_sliced(rule):
+    """A complete graph (every level one variable) with more replicas than fit
+    at once: speculative windows inside a time-sliced launch give the states,
+    energies, change counts and best states of the level-by-level plain waves."""
+    model = Model(wl.quio_complete(21, n=1500, lo=-40, hi=40))
+    tmax, tmin = model.default_temperatures()
+    S, R = 20, 2000
+    a = model.run(rule, S, R, seed=3, t_max=tmax, t_min=tmin, report=True, best=True)
+    b = model.run(rule, S, R, seed=3, t_max=tmax, t_min=tmin, report=True, best=True,
+                  flags=_lib.SA_FLAG_NO_SPECULATION | _lib.SA_FLAG_NO_TIME_SLICING)
+    assert a["report"]["time_sliced"] == 1 and b["report"]["time_sliced"] == 0, a["report"]
+    for key in ("states", "energies", "accepts", "best_states", "best_energies"):
+        assert torch.equal(a[key], b[key]), (rule, key)
+
+
+# ------------------------------------------------------------------ best states at sweep ends
+@pytest.mark.parametrize("rule", ALL_RULES)
+def test_best_states_integer_replay(rule):
+    """Integer models: the best state at sweep ends and its energy equal the
+    oracle's (trajectory replay), on a sparse QUIO and a higher-order model;
+    host and device outputs agree; the best energy is the best state's energy
+    and never above the final one."""
+    for inst in (wl.quio_sparse_int(31, n=600, n_edges=3000, lo=-20, hi=20),
+                 wl.random_small(32, n=60, max_order=4, lo=-5, hi=5, n_terms=300, coef_type="i32", cmax=6)):
+        model = Model(inst)
+        om = orc.Model(inst)
+        tmax, tmin = om.auto_temperatures()
+        S, R, TR = 40, 24, 4
+        trace = torch.zeros((S, TR, model.n), dtype=torch.int32, device="cuda")
+        out = model.run(rule, S, R, seed=8, t_max=tmax, t_min=tmin, trace=trace, trace_replicas=TR, best=True)
+        bst, ben = out["best_states"], out["best_energies"]
+        assert torch.equal(model.energy(bst), ben)
+        assert bool((ben <= out["energies"]).all())
+        # the same run into host buffers
+        hs = np.zeros((R, model.n), np.int32)
+        he = np.zeros(R, np.int64)
+        hb = np.zeros((R, model.n), np.int32)
+        hbe = np.zeros(R, np.int64)
+        p = make_params(rule, S, R, seed=8, t_max=tmax, t_min=tmin, best_states=hb, best_energies=hbe)
+        sa_run(model.handle, p, hs, he)
+        assert np.array_equal(hb, bst.cpu().numpy()) and np.array_equal(hbe, ben.cpu().numpy())
+        res = _oracle_follow(om, rule, S, 8, tmax, tmin, list(range(TR)), trace.cpu().numpy(), TR, best=True)
+        for r, x in enumerate(res):
+            assert x["follow"]["mismatch"] == 0, (rule, r, x["follow"])
+            assert np.array_equal(x["best_states"][0], hb[r]) and x["best_energy"][0] == hbe[r], (rule, r)
+
+
+@pytest.mark.parametrize("rule", ALL_RULES)
+def test_best_states_float(rule):
+    """Float models: the best energy is the FP64 energy of the best state, at
+    most the final energy (within the refresh tolerance) and the per-sweep
+    energies' minimum (same); speculative windows do not change it."""
+    inst = wl.batch_instance({"index": 0, "n": 150, "width": 30, "dense": True, "deg": 0, "seed": 13})
+    model = Model(inst)
+    tmax, tmin = model.default_temperatures()
+    S, R = 60, 32
+    et = torch.zeros((S, R), dtype=torch.float64, device="cuda")
+    out = model.run(rule, S, R, seed=5, t_max=tmax, t_min=tmin, energy_trace=et, best=True)
+    ref = model.run(rule, S, R, seed=5, t_max=tmax, t_min=tmin, best=True, flags=_lib.SA_FLAG_NO_SPECULATION)
+    for key in ("best_states", "best_energies"):
+        assert torch.equal(out[key], ref[key]), key
+    ben = out["best_energies"]
+    assert torch.equal(model.energy(out["best_states"]), ben)
+    tol = 1e-5 * out["energies"].abs().max().item()
+    assert bool((ben <= out["energies"] + tol).all())
+    torch.testing.assert_close(ben, et.min(dim=0).values, rtol=1e-5, atol=tol)
+
+
+def test_best_states_rejected_where_unsupported():
+    """Best-state outputs go in pairs, and batches, served requests and the
+    allocation-free entry point reject them."""
+    from paper_2511_17245_gb300 import (SAError, sa_batch_create, sa_run_noalloc, sa_server_create,
+                                        sa_server_destroy, sa_server_submit)
+    model = Model(wl.quio_dense_small(0))
+    bs = torch.zeros((4, model.n), dtype=torch.int32, device="cuda")
+    be = torch.zeros(4, dtype=torch.int64, device="cuda")
+    st = torch.zeros((4, model.n), dtype=torch.int32, device="cuda")
+    with pytest.raises(SAError) as e:
+        sa_run(model.handle, make_params("metropolis", 5, 4, best_states=bs), st, be)
+    assert e.value.status == 1
+    p = make_params("metropolis", 5, 4, best_states=bs, best_energies=be)
+    with pytest.raises(SAError) as e:
+        sa_run_noalloc(model.handle, p, st, torch.zeros(4, dtype=torch.int64, device="cuda"))
+    assert e.value.status == 3
+    with pytest.raises(SAError) as e:
+        sa_batch_create([model.handle], [p])
+    assert e.value.status == 3
+    srv = sa_server_create(1 << 30, 4)
+    try:
+        with pytest.raises(SAError) as e:
+            sa_server_submit(srv, model.handle, p)
+        assert e.value.status == 3
+    finally:
+        sa_server_destroy(srv)

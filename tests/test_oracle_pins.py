@@ -471,6 +471,25 @@ def test_run_matches_independent_python_sa(rule):
 
 
 @pytest.mark.parametrize("rule", ["metropolis", "heat_bath", "opt_metropolis"])
+def test_best_state_is_first_lowest_sweep_end(rule):
+    """The oracle's best state is, among the independent Python SA's states at
+    the ends of the sweeps, the first one of lowest energy (full recompute),
+    and its energy is that state's energy."""
+    inst = wl.random_small(43, n=5, max_order=3, lo=-2, hi=3, n_terms=14, coef_type="i32", cmax=4)
+    m = orc.Model(inst)
+    S, seed = 10, 0x55
+    for rep in range(3):
+        _, near, tr = _python_sa(inst, rule, S, seed, 15.0, 0.5, rep)
+        assert near == 0
+        ends = [_raw_energy(inst, tr[s].tolist()) for s in range(S)]
+        s_best = int(np.argmin(ends))                      # first lowest
+        res = m.run(rule, S, seed, 15.0, 0.5, r_begin=rep, r_end=rep + 1, best=True)
+        assert res["best_states"][0].tolist() == tr[s_best].tolist(), (rule, rep)
+        assert res["best_energy"][0] == ends[s_best] == min(ends)
+        assert res["best_energy"][0] <= res["energy"][0]
+
+
+@pytest.mark.parametrize("rule", ["metropolis", "heat_bath", "opt_metropolis"])
 def test_tracked_energy_equals_recomputed(rule):
     for inst in [wl.quio_dense_small(0), wl.random_small(5, n=8, max_order=4, lo=-3, hi=3, n_terms=30, coef_type="f64")]:
         m = orc.Model(inst)
