@@ -263,7 +263,10 @@ def run_batched_vs_plain(torch, hbm_gbs, sample_every=128, sweep_grid=(250, 500,
                is the time of the first count whose energy sum is <= E*;
       dense half  the 2,048 dense instances as their own batch: HBM fraction
                of their J-row reads (one row of N-1 (column, value) pairs, 8 B
-               each, per accepted change, counted from the change counts)."""
+               each, per accepted change, counted from the change counts);
+      other rules  heat bath and OTM, batched vs plain on every 8th dense and
+               every 8th sparse instance (512), the plain form timed on the
+               same 64 instances as above and scaled."""
     import concurrent.futures as cf
     from paper_2511_17245_gb300 import (Model, make_params, sa_batch_autotune, sa_batch_create, sa_batch_destroy,
                                         sa_batch_get_info, sa_batch_result, sa_batch_run, sa_run)
@@ -280,12 +283,12 @@ def run_batched_vs_plain(torch, hbm_gbs, sample_every=128, sweep_grid=(250, 500,
     st = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
-    def params_for(S, idx):
-        return [make_params("metropolis", S, 32, seed=0, instance_id=i, t_max=temps[i][0], t_min=temps[i][1])
+    def params_for(S, idx, rule="metropolis"):
+        return [make_params(rule, S, 32, seed=0, instance_id=i, t_max=temps[i][0], t_min=temps[i][1])
                 for i in idx]
 
-    def timed_batch(idx, S, tune):
-        b = sa_batch_create([models[i].handle for i in idx], params_for(S, idx))
+    def timed_batch(idx, S, tune, rule="metropolis"):
+        b = sa_batch_create([models[i].handle for i in idx], params_for(S, idx, rule))
         try:
             if tune:
                 sa_batch_autotune(b, 10, st.cuda_stream)
@@ -317,18 +320,26 @@ def run_batched_vs_plain(torch, hbm_gbs, sample_every=128, sweep_grid=(250, 500,
     att = grid[1000]["attempts"]
     # plain form on a stratified sample (instances alternate dense / sparse)
     sample = list(range(0, len(models), sample_every)) + list(range(1, len(models), sample_every))
-    plain_ms, rel = 0.0, []
-    for i in sample:
-        m, p = models[i], params_for(1000, [i])[0]
-        o_s = torch.empty((32, m.n), dtype=torch.int32, device="cuda")
-        o_e = torch.empty(32, dtype=torch.float64, device="cuda")
-        e0.record(st)
-        sa_run(m.handle, p, o_s, o_e, None, st.cuda_stream)
-        e1.record(st)
-        torch.cuda.synchronize()
-        plain_ms += e0.elapsed_time(e1)
-        pe = o_e.cpu().numpy()
-        rel.append(abs(en1000[i].mean() - pe.mean()) / max(1e-12, abs(pe.mean())))
+
+    def plain_time(rule, batched_en, pos):
+        """Total device time of one sa_run per sampled instance, and the
+        largest relative difference of its mean final energy from the batched
+        form's (`pos` maps an instance to its row in `batched_en`)."""
+        tot, diffs = 0.0, []
+        for i in sample:
+            m, p = models[i], params_for(1000, [i], rule)[0]
+            o_s = torch.empty((32, m.n), dtype=torch.int32, device="cuda")
+            o_e = torch.empty(32, dtype=torch.float64, device="cuda")
+            e0.record(st)
+            sa_run(m.handle, p, o_s, o_e, None, st.cuda_stream)
+            e1.record(st)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+            pe = o_e.cpu().numpy()
+            diffs.append(abs(batched_en[pos[i]].mean() - pe.mean()) / max(1e-12, abs(pe.mean())))
+        return tot, max(diffs)
+
+    plain_ms, rel_max = plain_time("metropolis", en1000, {i: i for i in everyone})
     plain_total_ms = plain_ms * len(models) / len(sample)
     _progress(f"batched: plain sample {plain_ms:.0f} ms")
     target = grid[1000]["energy_sum"]   # equal to the plain form's (same seeds; checked on the sample)
@@ -338,6 +349,18 @@ def run_batched_vs_plain(torch, hbm_gbs, sample_every=128, sweep_grid=(250, 500,
     dms, _, dacc, _ = timed_batch(dense, 1000, tune=True)
     row_bytes = sum(float(dacc[j].sum()) * (models[i].n - 1) * 8 for j, i in enumerate(dense))
     dense_gbs = row_bytes / (dms / 1e3) / 1e9
+    # heat bath and OTM on a stratified eighth of the instances
+    sub = list(range(0, len(models), 16)) + list(range(1, len(models), 16))
+    other = {}
+    for rule in ("heat_bath", "opt_metropolis"):
+        bms, ben, _, binfo = timed_batch(sub, 1000, tune=True, rule=rule)
+        pms, pdiff = plain_time(rule, ben, {i: j for j, i in enumerate(sub)})
+        p_total = pms * len(sub) / len(sample)
+        other[rule] = {"instances": len(sub), "batched_ms": bms, "batched_attempts_per_s": binfo["attempts"] / (bms / 1e3),
+                       "plain_ms_estimated": p_total, "plain_attempts_per_s": binfo["attempts"] / (p_total / 1e3),
+                       "speedup": p_total / bms, "final_energy_mean_rel_diff_max": float(pdiff),
+                       "launch_shape": {k: binfo[k] for k in ("threads_per_replica", "replicas_per_block", "blocks")}}
+        _progress(f"batched: {rule} on {len(sub)} instances {bms:.0f} ms, plain estimate {p_total:.0f} ms")
     for m in models:
         m.close()
     return {"workload": "4096 uneven QUIO instances, 32 replicas, 1000 sweeps, metropolis",
@@ -350,9 +373,12 @@ def run_batched_vs_plain(torch, hbm_gbs, sample_every=128, sweep_grid=(250, 500,
                                   "target": "sum of per-instance mean final energies of the plain form, 1000 sweeps",
                                   "batched_sweep_grid": {str(S): {"ms": grid[S]["ms"], "energy_sum": grid[S]["energy_sum"]}
                                                          for S in sweep_grid}},
-            "final_energy_mean_rel_diff_max": float(max(rel)), "launch_shape": grid[1000]["launch_shape"],
+            "final_energy_mean_rel_diff_max": float(rel_max), "launch_shape": grid[1000]["launch_shape"],
             "dense_half": {"instances": len(dense), "ms": dms, "row_bytes": row_bytes, "achieved_gbs": dense_gbs,
-                           "hbm_peak_gbs": hbm_gbs, "frac": dense_gbs / hbm_gbs}}
+                           "hbm_peak_gbs": hbm_gbs, "frac": dense_gbs / hbm_gbs},
+            "other_rules": {"instances": "every 8th dense and every 8th sparse instance (512), 1000 sweeps",
+                            "plain_sample": f"the same {len(sample)} instances, scaled by {len(sub) / len(sample):.0f}",
+                            **other}}
 
 
 def _progress(msg):
