@@ -568,6 +568,9 @@ def run_small_configs(torch, steps=2, warmup=1):
 
 
 # ---------------------------------------------------------------- GPU leg
+T_START = time.perf_counter()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -582,6 +585,8 @@ def main():
     ap.add_argument("--replicas", type=int, default=REPLICAS,
                     help="override for profiling a smaller case (bench numbers use the default)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--time-budget", type=float, default=1500.0,
+                    help="seconds the whole run may take; the other configurations' parts that would pass it are skipped")
     ap.add_argument("--quick", action="store_true",
                     help="only the benchmark workload: skip the dense 32-variable and Zipf HUIO runs, the "
                          "batched-vs-plain comparison and serving (several minutes together)")
@@ -732,10 +737,18 @@ def main():
     extended = None
     if rank == 0 and world == 1 and not args.quick:
         extended = {}
-        parts = [("small_configs", lambda: run_small_configs(torch)),
-                 ("batched_vs_plain", lambda: run_batched_vs_plain(torch, float(peaks.get("hbm_gbs", 6800.0)))),
-                 ("serving", lambda: run_serving(torch))]
-        for name, fn in parts:
+        # (name, function, longest wall time seen for the part, s): a part that
+        # could not end within the run's time budget is skipped and said so
+        parts = [("small_configs", lambda: run_small_configs(torch), 60),
+                 ("batched_vs_plain", lambda: run_batched_vs_plain(torch, float(peaks.get("hbm_gbs", 6800.0))), 600),
+                 ("serving", lambda: run_serving(torch), 720)]
+        for name, fn, longest in parts:
+            elapsed = time.perf_counter() - T_START
+            if elapsed + longest > args.time_budget:
+                extended[name] = {"skipped": f"{elapsed:.0f} s into the run, the part (up to {longest} s) would pass "
+                                             f"the {args.time_budget:.0f} s budget (--time-budget)"}
+                print(json.dumps({name: extended[name]}), file=sys.stderr, flush=True)
+                continue
             t_part = time.perf_counter()
             try:
                 extended[name] = fn()
